@@ -1,0 +1,144 @@
+"""Pins of the multi-level oracle (FLGF-AMR, Sec. 3.4; FIF-AMR, Sec. 3.5) against limits and identities
+that the paper and the mathematics fix, not against the oracle itself."""
+import numpy as np
+import pytest
+
+import lgf_synth as S
+import oracle
+from oracle import amr, core
+
+
+def _two_level_mesh(B=8, n_ext=4, h0=1.0):
+    lvl0 = S.box_blocks((24, 24, 24), B)
+    lvl1 = np.array([[2, 2, 2], [3, 2, 2], [2, 3, 2], [3, 3, 2], [2, 2, 3]], np.int32)
+    return dict(B=B, h0=h0, n_ext=n_ext, levels=[lvl0, lvl1])
+
+
+def _gaussian_levels(mesh, sigma=3.0, centre=(12.0, 12.0, 12.0)):
+    """Smooth source sampled at each level's cell centres (level-0 cell units for the geometry)."""
+    B = mesh["B"]
+    out = []
+    for k, blk in enumerate(mesh["levels"]):
+        h = 0.5 ** k
+        data = np.zeros((1, len(blk), B, B, B))
+        for i, (bx, by, bz) in enumerate(blk):
+            z, y, x = np.meshgrid(*[(B * b + np.arange(B) + 0.5) * h for b in (bz, by, bx)], indexing="ij")
+            r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2
+            data[0, i] = np.exp(-r2 / sigma ** 2)
+        out.append(data)
+    return out
+
+
+def test_single_level_reduces_to_lgf_solve():
+    rng = np.random.default_rng(2)
+    B = 8
+    blk = S.box_blocks((16, 24, 16), B)
+    f = rng.standard_normal((2, len(blk), B, B, B))
+    mesh = dict(B=B, h0=0.25, n_ext=4, levels=[blk])
+    out, masks = amr.flgf_amr(mesh, [f])
+    box = S.blocks_to_box(f, blk, B, (16, 24, 16))
+    ref = oracle.solve_box_fft(box, 0.25)
+    got = S.blocks_to_box(out[0], blk, B, (16, 24, 16))
+    assert masks[0].all()
+    assert np.abs(got - ref).max() < 1e-14 * np.abs(ref).max()
+
+
+def test_fine_only_sources_match_composite_definition_exactly():
+    # with fhat_0 = 0, psi_0 = 0 and the correction vanishes: steps 1-3 reduce to the definition
+    rng = np.random.default_rng(3)
+    mesh = _two_level_mesh()
+    B = mesh["B"]
+    f0 = np.zeros((1, len(mesh["levels"][0]), B, B, B))
+    f1 = rng.standard_normal((1, len(mesh["levels"][1]), B, B, B))
+    out, masks = amr.flgf_amr(mesh, [f0, f1])
+    comp = amr.composite_definition(mesh, [f0, f1])
+    for k in range(2):
+        scale = np.abs(comp[k][:, masks[k]]).max()
+        assert np.abs(out[k] - comp[k])[:, masks[k]].max() < 1e-13 * scale
+
+
+def test_interpolation_and_coarsening_on_linear_fields():
+    lc = amr.Level(0, (-3, -4, -2), (10, 12, 14), 1.0)
+    lf = amr.Level(1, (0, 0, 2), (8, 10, 12), 0.5)
+    z, y, x = np.meshgrid(*[lc.origin[a] + np.arange(n) + 0.5 for a, n in zip((2, 1, 0), lc.shape)],
+                          indexing="ij")
+    lin = (0.3 * x - 1.1 * y + 0.7 * z + 2.0)[None]
+    up = amr.interp_up(lin, lc, lf)
+    zf, yf, xf = np.meshgrid(*[(lf.origin[a] + np.arange(n) + 0.5) / 2 for a, n in zip((2, 1, 0), lf.shape)],
+                             indexing="ij")
+    ref = 0.3 * xf - 1.1 * yf + 0.7 * zf + 2.0
+    assert np.nanmax(np.abs(up[0] - ref)) < 1e-13 and np.isfinite(up).all()
+    # coarsening a fine linear field gives the linear field at the parent centres
+    down = amr.coarsen(ref[None], lf, lc)
+    cover = amr.coarsen_mask(np.ones(lf.shape, bool), lf, lc)
+    assert np.abs(down[0][cover] - lin[0][cover]).max() < 1e-13
+
+
+def test_correction_source_vanishes_for_linear_psi():
+    # S = P L_{k-1} - L_k P annihilates linear fields (P exact on them, both Laplacians zero)
+    lc = amr.Level(0, (0, 0, 0), (10, 10, 10), 1.0)
+    lf = amr.Level(1, (4, 4, 4), (8, 8, 8), 0.5)
+    z, y, x = np.meshgrid(*[np.arange(n) + 0.5 for n in lc.shape], indexing="ij")
+    psi = (2.0 * x - 0.5 * y + 0.25 * z)[None]
+    s = amr.interp_up(amr.laplacian_box(psi, 1.0), lc, lf) - amr.laplacian_box(amr.interp_up(psi, lc, lf), 0.5)
+    assert np.nanmax(np.abs(s)) < 1e-12
+
+
+def test_converges_to_composite_definition_as_extension_grows():
+    mesh = _two_level_mesh(n_ext=0)
+    f = _gaussian_levels(mesh)
+    errs = []
+    for ne in (0, 2, 6, 14):
+        mesh["n_ext"] = ne
+        out, masks = amr.flgf_amr(mesh, f)
+        comp = amr.composite_definition(mesh, f)
+        errs.append(np.abs(out[1] - comp[1])[:, masks[1]].max() / np.abs(comp[1][:, masks[1]]).max())
+    assert errs[-1] < errs[0] / 100 and errs[2] < errs[0]
+    assert errs[-1] < 3e-4  # the order of the paper's ~1e-4 cut-off at N_E = 14 (Sec. 3.4)
+
+
+def test_residual_identity_on_extended_region():
+    # L_k phi^k = F_k + P L_{k-1} psi_{k-1} wherever the correction source is kept (Eq. (eq:combine_S))
+    mesh = _two_level_mesh(n_ext=4)
+    f = _gaussian_levels(mesh)
+    rng = np.random.default_rng(8)
+    f[1] = f[1] + 0.1 * rng.standard_normal(f[1].shape)
+    out, masks, I = amr.flgf_amr(mesh, f, return_internals=True)
+    lv, phi, psi, F = I["levels"], I["phi"], I["psi"], I["F"]
+    lhs = amr.laplacian_box(phi[1], lv[1].h)
+    rhs = F[1] + amr.interp_up(amr.laplacian_box(psi[0], lv[0].h), lv[0], lv[1])
+    region = lv[1].omega | I["steps"][0]["ext"]
+    inner = region & ~amr.dilate_maxnorm(~region, 1)
+    d = np.abs(lhs - rhs)[:, inner]
+    assert np.isfinite(d).all() and d.max() < 1e-10 * np.abs(rhs[:, inner]).max()
+
+
+def test_heat_single_level_reduces_to_heat_kernel():
+    rng = np.random.default_rng(6)
+    B = 8
+    blk = S.box_blocks((16, 16, 24), B)
+    f = rng.standard_normal((1, len(blk), B, B, B))
+    mesh = dict(B=B, h0=1.0, n_ext=4, levels=[blk])
+    g = amr.fif_amr(mesh, [f], 0.1)[0]
+    box = S.blocks_to_box(f, blk, B, (16, 16, 24))
+    ref = oracle.heat_box(box, 0.1)
+    assert np.abs(S.blocks_to_box(g, blk, B, (16, 16, 24)) - ref).max() < 1e-15 * np.abs(ref).max() + 1e-300
+
+
+def test_heat_preserves_constants_away_from_level_boundaries():
+    B = 8
+    mesh = dict(B=B, h0=1.0, n_ext=4, levels=[S.box_blocks((40, 40, 40), B),
+                                              np.array([[4, 4, 4], [5, 4, 4], [4, 5, 5]], np.int32)])
+    f = [np.ones((1, len(b), B, B, B)) for b in mesh["levels"]]
+    g = amr.fif_amr(mesh, f, 0.1)
+    lv = amr.build_levels(mesh)
+    # P_0 fhat = 1 on every level-0 user cell (own values on Omega_0, 8-child means of 1 under
+    # level 1), so the kernel returns 1 on Omega_0 cells more than its radius from the user boundary
+    om = lv[0].omega
+    w = core.heat_weights_1d(0.1 / 4)
+    deep = om & ~amr.dilate_maxnorm(~lv[0].user, len(w) + 1)
+    box = np.zeros((1,) + lv[0].shape)
+    for i, b in enumerate(mesh["levels"][0]):
+        box[(slice(None),) + lv[0].block_slice(b, B)] = g[0][:, i]
+    assert deep.sum() > 100
+    assert np.abs(box[0][deep] - 1.0).max() < 1e-14
