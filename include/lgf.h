@@ -1,0 +1,184 @@
+/*
+ * lgf.h -- C ABI of a GB300 (sm_103a) library for the free-space 7-point Poisson solve and the
+ * discrete heat-kernel (integrating-factor) apply on block-structured multi-level meshes, after
+ * Yu, Dorschner & Colonius, "Multi-resolution lattice Green's function method for incompressible
+ * flows" (J. Comput. Phys., 2020).
+ *
+ * Problem statement (Sec. 2.2, Eqs. (eq:discrete_laplace)-(eq:lgf_convolution)): on a lattice of
+ * spacing h, L_h phi = f with phi -> 0 at infinity, L_h the 7-point Laplacian
+ * h^-2 (sum_{+-e_i} phi(n +- e_i) - 6 phi(n)).  The unique decaying solution is the lattice
+ * convolution phi = h^2 (G * f) with the lattice Green's function G (L_1 G = delta).  On a composite
+ * mesh of levels k = 0..K-1 (h_k = h_0 / 2^k, level 0 coarsest, Sec. 3.1) the solve follows the
+ * FLGF-AMR algorithm of Sec. 3.4 (Eqs. (eq:combine_S)-(eq:FLGF-AMR)); the heat apply follows
+ * FIF-AMR, Sec. 3.5 (Eq. (eq:FIF-AMR)).
+ *
+ * Conventions shared by every call
+ *  - Blocks are B^3 cells (B in {8, 16}).  Block (bx, by, bz) of level k holds the level-k cells
+ *    B*(bx, by, bz) + [0, B)^3.  Field arrays are laid out [ncomp][sum_k nblocks_k][B][B][B]
+ *    (blocks in mesh order, level 0 first; inside a block z slowest, x fastest).
+ *  - Omega_k (the cells where level k holds the solution) is every cell of a level-k block that no
+ *    level-(k+1) block covers; every level-(k+1) block must lie inside level-k blocks (nesting).
+ *  - Pointers named *_dev are DEVICE pointers owned by the caller; pointers without the suffix are
+ *    HOST pointers owned by the caller and only read during the call.
+ *  - Every call is asynchronous on the given CUDA stream (NULL = the legacy default stream) unless
+ *    documented otherwise; outputs are valid once the stream reaches the end of the call's work.
+ *  - Status: 0 (LGF_OK) on success, a negative LGF_E_* otherwise.  Nothing is thrown across the ABI.
+ *    lgf_last_error() returns a thread-local message for the last failing call of that thread.
+ *    On error, output contents are unspecified.
+ */
+#ifndef LGF_H
+#define LGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define LGF_OK 0
+#define LGF_E_INVALID_ARG (-1)  /* null pointer, bad size, unsupported enum value */
+#define LGF_E_MESH (-2)         /* mesh not nested, duplicate blocks, block size mismatch */
+#define LGF_E_TABLE_RANGE (-3)  /* the table does not cover a block offset the mesh needs */
+#define LGF_E_OOM (-4)          /* device allocation failed */
+#define LGF_E_CUDA (-5)         /* a CUDA runtime call or kernel launch failed */
+#define LGF_E_TIMEOUT (-6)      /* a bounded device-side wait gave up (batched scheduler) */
+#define LGF_E_PRECISION (-7)    /* FP64 residual above opts->residual_tol */
+#define LGF_E_UNSUPPORTED (-8)  /* valid request this build does not implement */
+
+/* ---- storage types of caller fields */
+#define LGF_F64 0
+#define LGF_F32 1
+
+/* ---- arithmetic of the convolution path
+ *  FP64 : native double everywhere.
+ *  FP32 : plain single precision (error ~1e-6 relative; reported, not a 1e-10 path).
+ *  DF32 : "mixed": FP32 hardware, every value a pair of floats (hi + lo) with error-free products
+ *         (fmaf) and sums, about 44 significant bits; the FP64 residual is the acceptance check. */
+#define LGF_PREC_FP64 0
+#define LGF_PREC_FP32 1
+#define LGF_PREC_DF32 2
+
+/* ---- how the per-frequency sum over block pairs is evaluated
+ *  PAIR : direct sum over every (target, source) block pair with per-offset kernel spectra.
+ *  BOX  : the same sum, diagonalised by a zero-padded FFT over each level's block grid.
+ *  AUTO : the autotuner's choice from the pair count and grid fill. */
+#define LGF_MAC_AUTO 0
+#define LGF_MAC_PAIR 1
+#define LGF_MAC_BOX 2
+
+/* ---- table flags: which spectrum formats lgf_table_create keeps on the device */
+#define LGF_TBL_FP64 1u
+#define LGF_TBL_FP32 2u
+#define LGF_TBL_DF32 4u
+
+typedef struct lgf_table lgf_table; /* opaque: device LGF values + kernel spectra + workspaces */
+
+typedef struct lgf_mesh {
+  int32_t nlevels;            /* K >= 1 */
+  int32_t block;              /* B, equal to the table's block size */
+  double h0;                  /* level-0 spacing (> 0); h_k = h0 / 2^k */
+  const int32_t *nblocks;     /* host [K]: blocks per level (>= 1 each) */
+  const int32_t *block_ijk;   /* host [sum nblocks][3]: (bx, by, bz) per block, level by level */
+  const uint8_t *block_role;  /* host [sum nblocks] or NULL (= all 3).  bit0: the block carries
+                                 source values; bit1: the block receives output.  Honoured for
+                                 K = 1; for K > 1 every block is both. */
+  int32_t n_ext;              /* N_E >= 0: width in cells of the extended correction region
+                                 Omega_k^E (Eq. (eq:extended_regions), max-norm, whole cells) */
+} lgf_mesh;
+
+typedef struct lgf_solve_opts {
+  int32_t precision;     /* LGF_PREC_* */
+  int32_t mac_mode;      /* LGF_MAC_* */
+  int32_t residual;      /* 1: compute the FP64 residual into the report (synchronises) */
+  int32_t timing;        /* 1: time the phases with CUDA events into the report (synchronises) */
+  double residual_tol;   /* > 0 with residual = 1: LGF_E_PRECISION when residual_rel exceeds it */
+} lgf_solve_opts;
+
+typedef struct lgf_report {
+  double ms_total;        /* with timing = 1: wall time of the call's device work */
+  double ms_phase[8];     /* restrict, correction, forward, mac, inverse, interp, residual, heat */
+  double residual_rel;    /* max |L_k phi - source| / max |source| over interior output cells */
+  int64_t target_cells;   /* cells written (sum over levels of |Omega_k| or target blocks) */
+  int64_t source_blocks;  /* blocks forward-transformed, summed over levels and source sets */
+  int64_t target_blocks;  /* blocks inverse-transformed */
+  int64_t pairs;          /* block pairs summed by the PAIR mode (0 for BOX) */
+  int64_t scratch_bytes;  /* device workspace held by the table for this stream */
+  int64_t kernel_launches;/* kernels this call launched */
+  int32_t mac_mode_used;  /* LGF_MAC_PAIR or LGF_MAC_BOX */
+  int32_t reserved;
+} lgf_report;
+
+/*
+ * lgf_table_create -- tabulate the unit-lattice LGF and the kernel spectra (Sec. 5: the LGF is
+ * evaluated once at start-up and stored).
+ *   out              : receives the new table (caller destroys it with lgf_table_destroy).
+ *   block            : B (8 or 16).
+ *   max_block_offset : host [3]; spectra are kept for every block offset o with |o_a| <= this,
+ *                      and G for every lattice offset up to B*(max+1) per axis.  A mesh level
+ *                      whose block extent along axis a exceeds max_block_offset[a] + 1 (after
+ *                      adding the blocks the solve needs around Omega_k^E) is rejected with
+ *                      LGF_E_TABLE_RANGE.
+ *   flags            : OR of LGF_TBL_*; the precisions a solve may use must be present.
+ *   cuda_stream      : stream for the generation kernels; the call synchronises it before
+ *                      returning, so the table is ready for use on any stream.
+ * G(n) = -int_0^inf prod_i e^{-2t} I_{n_i}(2t) dt is computed in FP64 on the device (composite
+ * Gauss-Legendre quadrature in ln t with the large-t Hankel tail).
+ */
+int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_offset[3],
+                     uint32_t flags, void *cuda_stream);
+
+/* lgf_table_destroy -- release a table and every workspace it holds (synchronises the device). */
+int lgf_table_destroy(lgf_table *t);
+
+/*
+ * lgf_table_lgf_values -- copy G on the lattice octant [0, n]^3 into host memory
+ * (host_out[(c*(n+1) + b)*(n+1) + a] = G(a, b, c)); n must not exceed the table's lattice extent.
+ * Synchronous.  For tests and diagnostics.
+ */
+int lgf_table_lgf_values(const lgf_table *t, int32_t n, double *host_out);
+
+/*
+ * lgf_poisson_solve -- free-space solve of L phi = f on the composite mesh (Sec. 3.4 FLGF-AMR:
+ * cumulative coarsening of the sources, level-by-level convolution with the commutation source
+ * correction S psi_{k-1} on Omega_k and Omega_k^E, interpolation of the coarser solution, and
+ * restriction to Omega_k).
+ *   ncomp   : number of independent scalar components (>= 1), e.g. 3 for a vector Poisson.
+ *   f_dev   : device [ncomp][sum nblocks][B^3] source in `dtype`; values outside Omega_k (and of
+ *             blocks without the source role) are ignored.
+ *   phi_dev : device [ncomp][sum nblocks][B^3] output in `dtype`; written on Omega_k of blocks
+ *             with the target role, left untouched elsewhere.  Must not alias f_dev.
+ *   dtype   : LGF_F64 or LGF_F32 storage of f and phi (independent of opts->precision).
+ *   opts    : may be NULL (FP64, AUTO, no residual, no timing).
+ *   rep     : may be NULL.
+ */
+int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev,
+                      void *phi_dev, int32_t dtype, const lgf_solve_opts *opts, lgf_report *rep,
+                      void *cuda_stream);
+
+/*
+ * lgf_heat_apply -- integrating-factor apply (Sec. 2.3 Eq. (eq:IF-single); Sec. 3.5 FIF-AMR):
+ * g_k = Gamma_k [ E_{alpha_k} * (P_k fhat) ] with E_alpha(n) = prod_i e^{-2 alpha} I_{|n_i|}(2 alpha),
+ * alpha_k = alpha_finest * 4^{-(K-1-k)} (Eq. (eq:composite-LGF-IF)), P_k fhat the reconstruction of
+ * the AMR data on level k (own values, interpolation from coarser, coarsening from finer levels).
+ *   t            : may be NULL (the heat kernel needs no LGF table); when non-NULL its workspace
+ *                  pool is used.
+ *   alpha_finest : kappa*dt/h_finest^2 >= 0.
+ *   f_dev, g_dev : as for lgf_poisson_solve; g written on Omega_k.
+ * Only opts->precision (FP64 or FP32; DF32 runs as FP64) and opts->timing are read.
+ */
+int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev,
+                   void *g_dev, int32_t dtype, double alpha_finest, const lgf_solve_opts *opts,
+                   lgf_report *rep, void *cuda_stream);
+
+/* lgf_last_error -- message for the last non-zero status returned on the calling thread. */
+const char *lgf_last_error(void);
+
+/* lgf_version -- library version string. */
+const char *lgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGF_H */

@@ -1,0 +1,172 @@
+// api.cu -- the C ABI (include/lgf.h): table lifetime, argument checking, workspaces, dispatch.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <set>
+#include <tuple>
+
+#include "internal.h"
+#include "solver.h"
+
+namespace lgf {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+Workspace *workspace_for(lgf_table *t, cudaStream_t st) {
+  std::lock_guard<std::mutex> g(t->mu);
+  auto it = t->ws.find((void *)st);
+  if (it != t->ws.end()) return it->second;
+  Workspace *w = new Workspace();
+  t->ws[(void *)st] = w;
+  return w;
+}
+
+int check_mesh(const lgf_mesh *m, int B_expected) {
+  if (!m) return set_error(LGF_E_INVALID_ARG, "mesh is NULL");
+  if (m->nlevels < 1 || m->nlevels > 16) return set_error(LGF_E_INVALID_ARG, "nlevels %d", m->nlevels);
+  if (B_expected && m->block != B_expected)
+    return set_error(LGF_E_MESH, "mesh block %d differs from the table's %d", m->block, B_expected);
+  if (m->block != 8 && m->block != 16) return set_error(LGF_E_UNSUPPORTED, "block size %d", m->block);
+  if (!(m->h0 > 0.0)) return set_error(LGF_E_INVALID_ARG, "h0 must be > 0");
+  if (!m->nblocks || !m->block_ijk) return set_error(LGF_E_INVALID_ARG, "nblocks/block_ijk NULL");
+  if (m->n_ext < 0) return set_error(LGF_E_INVALID_ARG, "n_ext < 0");
+  int64_t off = 0;
+  for (int k = 0; k < m->nlevels; ++k) {
+    if (m->nblocks[k] < 1) return set_error(LGF_E_MESH, "level %d has no blocks", k);
+    std::set<std::tuple<int, int, int>> seen;
+    for (int i = 0; i < m->nblocks[k]; ++i) {
+      const int32_t *b = m->block_ijk + 3 * (off + i);
+      if (!seen.insert(std::make_tuple(b[0], b[1], b[2])).second)
+        return set_error(LGF_E_MESH, "duplicate block (%d,%d,%d) on level %d", b[0], b[1], b[2], k);
+    }
+    off += m->nblocks[k];
+  }
+  return LGF_OK;
+}
+
+}  // namespace lgf
+
+using namespace lgf;
+
+extern "C" {
+
+const char *lgf_last_error(void) { return g_last_error.c_str(); }
+const char *lgf_version(void) { return "lgf-gb300 0.1 (sm_103a)"; }
+
+int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_offset[3], uint32_t flags,
+                     void *cuda_stream) {
+  if (!out || !max_block_offset) return set_error(LGF_E_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (block != 8 && block != 16) return set_error(LGF_E_UNSUPPORTED, "block size %d", block);
+  for (int a = 0; a < 3; ++a)
+    if (max_block_offset[a] < 0 || max_block_offset[a] > 64)
+      return set_error(LGF_E_INVALID_ARG, "max_block_offset[%d] = %d out of [0, 64]", a, max_block_offset[a]);
+  if ((flags & 7u) == 0) return set_error(LGF_E_INVALID_ARG, "no spectrum format requested");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  lgf_table *t = new lgf_table();
+  cudaGetDevice(&t->device);
+  t->B = block;
+  t->mo = make_int3(max_block_offset[0], max_block_offset[1], max_block_offset[2]);
+  t->noff = (2 * t->mo.x + 1) * (2 * t->mo.y + 1) * (2 * t->mo.z + 1);
+  int mmax = std::max(t->mo.x, std::max(t->mo.y, t->mo.z));
+  t->N = block * (mmax + 1);
+  t->flags = flags;
+  int rc = build_lgf_octant(t->N, &t->Gd, st, &t->quad_T, &t->quad_nodes);
+  if (rc) {
+    delete t;
+    return rc;
+  }
+  const size_t W = (size_t)(2 * block) * (2 * block) * (block + 1);
+  const size_t n = W * t->noff;
+  if ((flags & LGF_TBL_FP64) && cudaMalloc(&t->s64, n * 16) != cudaSuccess) rc = LGF_E_OOM;
+  if (!rc && (flags & LGF_TBL_FP32) && cudaMalloc(&t->s32, n * 8) != cudaSuccess) rc = LGF_E_OOM;
+  if (!rc && (flags & LGF_TBL_DF32) && cudaMalloc(&t->sdf, n * 16) != cudaSuccess) rc = LGF_E_OOM;
+  if (rc) {
+    cudaGetLastError();
+    lgf_table_destroy(t);
+    return set_error(LGF_E_OOM, "spectra allocation (%zu offsets) failed", (size_t)t->noff);
+  }
+  rc = build_spectra(block, t->Gd, t->N + 1, t->mo, t->noff, t->s64, t->s32, t->sdf, st);
+  if (rc) {
+    lgf_table_destroy(t);
+    return rc;
+  }
+  *out = t;
+  return LGF_OK;
+}
+
+int lgf_table_destroy(lgf_table *t) {
+  if (!t) return LGF_OK;
+  cudaDeviceSynchronize();
+  if (t->Gd) cudaFree(t->Gd);
+  if (t->s64) cudaFree(t->s64);
+  if (t->s32) cudaFree(t->s32);
+  if (t->sdf) cudaFree(t->sdf);
+  for (auto &kv : t->ws) {
+    for (auto &b : kv.second->buf) b.release();
+    delete kv.second;
+  }
+  delete t;
+  return LGF_OK;
+}
+
+int lgf_table_lgf_values(const lgf_table *t, int32_t n, double *host_out) {
+  if (!t || !host_out) return set_error(LGF_E_INVALID_ARG, "NULL argument");
+  if (n < 0 || n > t->N) return set_error(LGF_E_TABLE_RANGE, "n = %d beyond the table extent %d", n, t->N);
+  const size_t K = (size_t)t->N + 1, k = (size_t)n + 1;
+  for (size_t c = 0; c < k; ++c)
+    for (size_t b = 0; b < k; ++b)
+      if (cudaMemcpy(host_out + (c * k + b) * k, t->Gd + (c * K + b) * K, k * sizeof(double),
+                     cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_error(LGF_E_CUDA, "copy of the LGF octant failed");
+  return LGF_OK;
+}
+
+int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev, void *phi_dev,
+                      int32_t dtype, const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream) {
+  if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");
+  int rc = check_mesh(m, t->B);
+  if (rc) return rc;
+  if (ncomp < 1) return set_error(LGF_E_INVALID_ARG, "ncomp %d", ncomp);
+  if (!f_dev || !phi_dev) return set_error(LGF_E_INVALID_ARG, "field pointer NULL");
+  if (f_dev == phi_dev) return set_error(LGF_E_INVALID_ARG, "f and phi alias");
+  if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0};
+  if (opts) o = *opts;
+  if (o.precision < 0 || o.precision > 2) return set_error(LGF_E_INVALID_ARG, "precision %d", o.precision);
+  if (o.mac_mode < 0 || o.mac_mode > 2) return set_error(LGF_E_INVALID_ARG, "mac_mode %d", o.mac_mode);
+  if (rep) memset(rep, 0, sizeof(*rep));
+  return solve_poisson(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream);
+}
+
+int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev, void *g_dev,
+                   int32_t dtype, double alpha_finest, const lgf_solve_opts *opts, lgf_report *rep,
+                   void *cuda_stream) {
+  int rc = check_mesh(m, t ? t->B : 0);
+  if (rc) return rc;
+  if (ncomp < 1) return set_error(LGF_E_INVALID_ARG, "ncomp %d", ncomp);
+  if (!f_dev || !g_dev) return set_error(LGF_E_INVALID_ARG, "field pointer NULL");
+  if (f_dev == g_dev) return set_error(LGF_E_INVALID_ARG, "f and g alias");
+  if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
+  if (!(alpha_finest >= 0.0) || alpha_finest > 1e4)
+    return set_error(LGF_E_INVALID_ARG, "alpha_finest %g", alpha_finest);
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0};
+  if (opts) o = *opts;
+  if (rep) memset(rep, 0, sizeof(*rep));
+  return solve_heat(t, m, ncomp, f_dev, g_dev, dtype, alpha_finest, o, rep, (cudaStream_t)cuda_stream);
+}
+
+}  // extern "C"

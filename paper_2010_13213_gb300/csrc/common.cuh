@@ -1,0 +1,179 @@
+// common.cuh -- arithmetic types shared by the library's kernels.
+//
+// Three arithmetics run the convolution path:
+//   double : native FP64 (GB300 runs it at 1/64 of the FP32 rate);
+//   float  : plain FP32;
+//   df     : "double-float": a value is the unevaluated sum hi + lo of two floats with
+//            |lo| <= ulp(hi)/2.  Sums use Knuth's TwoSum and products Dekker/Kahan's TwoProd through
+//            fmaf, so every elementary operation is error-free up to the final renormalisation
+//            (about 44-48 significant bits).  All float operations go through __f*_rn intrinsics so
+//            the compiler never contracts or reorders them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define LGF_HD __host__ __device__ __forceinline__
+#define LGF_D __device__ __forceinline__
+
+struct df {
+  float hi, lo;
+};
+
+LGF_D df df_make(double v) {
+  float h = __double2float_rn(v);
+  float l = __double2float_rn(v - (double)h);
+  return {h, l};
+}
+LGF_D double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+LGF_D df df_add(df a, df b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float hi = __fadd_rn(s, e);
+  float lo = __fsub_rn(e, __fsub_rn(hi, s));
+  return {hi, lo};
+}
+LGF_D df df_neg(df a) { return {-a.hi, -a.lo}; }
+LGF_D df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+LGF_D df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float hi = __fadd_rn(p, e);
+  float lo = __fsub_rn(e, __fsub_rn(hi, p));
+  return {hi, lo};
+}
+LGF_D df df_scale2(df a, float s) {  // exact when s is a power of two
+  return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
+}
+
+LGF_D df operator+(df a, df b) { return df_add(a, b); }
+LGF_D df operator-(df a, df b) { return df_sub(a, b); }
+LGF_D df operator*(df a, df b) { return df_mul(a, b); }
+LGF_D df operator-(df a) { return df_neg(a); }
+
+// ------------------------------------------------------------------ scalar traits
+template <class R>
+struct RT;
+template <>
+struct RT<double> {
+  LGF_D static double from(double v) { return v; }
+  LGF_D static double from(float v) { return (double)v; }
+  LGF_D static double to_d(double v) { return v; }
+  LGF_D static float to_f(double v) { return (float)v; }
+  LGF_D static double zero() { return 0.0; }
+  LGF_D static double half(double v) { return 0.5 * v; }
+  LGF_D static double scale(double v, double s) { return v * s; }
+};
+template <>
+struct RT<float> {
+  LGF_D static float from(double v) { return (float)v; }
+  LGF_D static float from(float v) { return v; }
+  LGF_D static double to_d(float v) { return (double)v; }
+  LGF_D static float to_f(float v) { return v; }
+  LGF_D static float zero() { return 0.0f; }
+  LGF_D static float half(float v) { return 0.5f * v; }
+  LGF_D static float scale(float v, double s) { return v * (float)s; }
+};
+template <>
+struct RT<df> {
+  LGF_D static df from(double v) { return df_make(v); }
+  LGF_D static df from(float v) { return {v, 0.0f}; }
+  LGF_D static double to_d(df v) { return df_to_double(v); }
+  LGF_D static float to_f(df v) { return __fadd_rn(v.hi, v.lo); }
+  LGF_D static df zero() { return {0.0f, 0.0f}; }
+  LGF_D static df half(df v) { return df_scale2(v, 0.5f); }
+  LGF_D static df scale(df v, double s) { return df_mul(v, df_make(s)); }
+};
+
+// ------------------------------------------------------------------ complex
+template <class R>
+struct cx {
+  R re, im;
+};
+template <class R>
+LGF_D cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+LGF_D cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+LGF_D cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R>
+LGF_D cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+template <class R>
+LGF_D cx<R> cx_zero() { return {RT<R>::zero(), RT<R>::zero()}; }
+
+// Twiddles W_64^j = cos(2 pi j / 64) - i sin(2 pi j / 64), j < 64, passed by value as a kernel
+// parameter (constant bank, broadcast to the warp).  Built on the host from sincospi in FP64.
+template <class R>
+struct Tw64 {
+  R c[64];
+  R s[64];
+};
+
+// W_N^k (forward: e^{-2 pi i k/N}; inverse: conjugate), N a power of two dividing 64.
+template <class R, int N, bool INV>
+LGF_D cx<R> twiddle(const Tw64<R> &tw, int k) {
+  const int j = (k * (64 / N)) & 63;
+  return INV ? cx<R>{tw.c[j], tw.s[j]} : cx<R>{tw.c[j], -tw.s[j]};
+}
+
+template <int N>
+LGF_HD constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// In-register radix-2 decimation-in-time FFT of length N (power of two <= 64), unnormalised.
+template <class R, int N, bool INV>
+LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int j = bitrev<N>(i);
+    if (j > i) {
+      cx<R> t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int len = 2; len <= N; len <<= 1) {
+#pragma unroll
+    for (int i = 0; i < N; i += len) {
+#pragma unroll
+      for (int j = 0; j < len / 2; ++j) {
+        cx<R> u = x[i + j];
+        cx<R> v = x[i + j + len / 2];
+        if (j != 0) v = v * twiddle<R, 64, INV>(tw, j * (64 / len));
+        x[i + j] = u + v;
+        x[i + j + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ loads/stores of fields
+// dtype 0: double storage, 1: float storage, 2: the kernel's own arithmetic type R (internal buffers).
+template <class R>
+LGF_D R load_field(const void *p, int64_t i, int dtype) {
+  if (dtype == 0) return RT<R>::from(((const double *)p)[i]);
+  if (dtype == 1) return RT<R>::from(((const float *)p)[i]);
+  return ((const R *)p)[i];
+}
+template <class R>
+LGF_D void store_field(void *p, int64_t i, int dtype, R v) {
+  if (dtype == 0)
+    ((double *)p)[i] = RT<R>::to_d(v);
+  else if (dtype == 1)
+    ((float *)p)[i] = RT<R>::to_f(v);
+  else
+    ((R *)p)[i] = v;
+}

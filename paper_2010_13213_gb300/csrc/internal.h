@@ -1,0 +1,134 @@
+// internal.h -- declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lgf.h"
+#include "common.cuh"
+
+namespace lgf {
+
+int set_error(int code, const char *fmt, ...);
+
+// Twiddles W_64^j from long-double cos/sin of the first octant and exact symmetries.
+template <class R>
+inline R tw_from_double(double v);
+template <>
+inline double tw_from_double<double>(double v) { return v; }
+template <>
+inline float tw_from_double<float>(double v) { return (float)v; }
+template <>
+inline df tw_from_double<df>(double v) {
+  float h = (float)v;
+  return df{h, (float)(v - (double)h)};
+}
+
+inline void tw64_double(double *c, double *s) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  double cq[17], sq[17];
+  for (int j = 0; j <= 16; ++j) {
+    cq[j] = (double)cosl(2.0L * pi * (long double)j / 64.0L);
+    sq[j] = (double)sinl(2.0L * pi * (long double)j / 64.0L);
+  }
+  cq[16] = 0.0;
+  sq[16] = 1.0;
+  cq[0] = 1.0;
+  sq[0] = 0.0;
+  for (int j = 0; j < 64; ++j) {
+    const int q = j / 16, r = j % 16;
+    double cr = cq[r], sr = sq[r];
+    switch (q) {
+      case 0: c[j] = cr; s[j] = sr; break;
+      case 1: c[j] = -sr; s[j] = cr; break;
+      case 2: c[j] = -cr; s[j] = -sr; break;
+      default: c[j] = sr; s[j] = -cr; break;
+    }
+  }
+}
+
+template <class R>
+inline Tw64<R> make_tw64() {
+  double c[64], s[64];
+  tw64_double(c, s);
+  Tw64<R> t;
+  for (int j = 0; j < 64; ++j) {
+    t.c[j] = tw_from_double<R>(c[j]);
+    t.s[j] = tw_from_double<R>(s[j]);
+  }
+  return t;
+}
+
+// table.cu
+int build_lgf_octant(int N, double **Gd_out, cudaStream_t st, double *quad_T, int *quad_nodes);
+int build_spectra(int B, const double *Gd, int K, int3 mo, int noff, void *s64, void *s32, void *sdf,
+                  cudaStream_t st);
+
+// pair_*.cu: launch wrappers, one instantiation per arithmetic
+template <class R>
+struct PairOps {
+  static int forward(int B, const void *f, int dtype, int64_t comp_stride, const int32_t *src_idx,
+                     int nsrc, int ncomp, void *spec, cudaStream_t st);
+  static int inverse(int B, const void *spec, int ntgt, int ncomp, const int32_t *tgt_idx, void *out,
+                     int dtype, int64_t comp_stride, const void *addend, int add_dtype, double scale,
+                     cudaStream_t st);
+  static int mac(int B, const void *F, int nsrc, const int4 *src_c, const void *Gh, int3 mo,
+                 void *Phi, int ntgt, const int4 *tgt_c, int ncomp, int accumulate, cudaStream_t st);
+};
+
+// Growable device buffer (never shrinks; freed with the owner).
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  int reserve(size_t n) {
+    if (n <= bytes) return LGF_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(LGF_E_OOM, "device allocation of %zu bytes failed", n);
+    }
+    bytes = n;
+    return LGF_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+// Per-stream scratch held by a table.
+struct Workspace {
+  DevBuf buf[16];
+  size_t total() const {
+    size_t s = 0;
+    for (auto &b : buf) s += b.bytes;
+    return s;
+  }
+};
+
+}  // namespace lgf
+
+struct lgf_table {
+  int B = 0;
+  int3 mo{0, 0, 0};  // max block offset per axis
+  int noff = 0;
+  int N = 0;         // lattice octant extent: G on [0, N]^3
+  double quad_T = 0.0;
+  int quad_nodes = 0;
+  unsigned flags = 0;
+  int device = 0;
+  double *Gd = nullptr;        // [N+1]^3 octant, FP64
+  void *s64 = nullptr;         // [noff][W] cx<double>
+  void *s32 = nullptr;         // [noff][W] cx<float>
+  void *sdf = nullptr;         // [noff][W] cx<df>
+  std::mutex mu;
+  std::map<void *, lgf::Workspace *> ws;  // keyed by stream
+};

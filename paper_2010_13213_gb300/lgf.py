@@ -1,0 +1,165 @@
+"""ctypes binding of ``liblgf.so`` (include/lgf.h): argument marshalling only.
+
+Every function keeps the C name.  Device buffers are passed as integer addresses (for instance
+``torch.Tensor.data_ptr()``) and streams as integer handles (``torch.cuda.Stream.cuda_stream``, 0 for
+the legacy default stream).  A non-zero status raises :class:`LgfError` carrying ``lgf_last_error()``.
+The library must have been built (``paper_2010_13213_gb300.build``); a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint8, c_uint32, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblgf.so")
+
+LGF_OK = 0
+LGF_E_INVALID_ARG = -1
+LGF_E_MESH = -2
+LGF_E_TABLE_RANGE = -3
+LGF_E_OOM = -4
+LGF_E_CUDA = -5
+LGF_E_TIMEOUT = -6
+LGF_E_PRECISION = -7
+LGF_E_UNSUPPORTED = -8
+LGF_F64, LGF_F32 = 0, 1
+LGF_PREC_FP64, LGF_PREC_FP32, LGF_PREC_DF32 = 0, 1, 2
+LGF_MAC_AUTO, LGF_MAC_PAIR, LGF_MAC_BOX = 0, 1, 2
+LGF_TBL_FP64, LGF_TBL_FP32, LGF_TBL_DF32 = 1, 2, 4
+PHASES = ("restrict", "correction", "forward", "mac", "inverse", "interp", "residual", "heat")
+
+
+class LgfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lgf status {status}: {msg}")
+        self.status = status
+
+
+class lgf_mesh(ctypes.Structure):
+    _fields_ = [("nlevels", c_int32), ("block", c_int32), ("h0", c_double),
+                ("nblocks", POINTER(c_int32)), ("block_ijk", POINTER(c_int32)),
+                ("block_role", POINTER(c_uint8)), ("n_ext", c_int32)]
+
+
+class lgf_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("mac_mode", c_int32), ("residual", c_int32),
+                ("timing", c_int32), ("residual_tol", c_double)]
+
+
+class lgf_report(ctypes.Structure):
+    _fields_ = [("ms_total", c_double), ("ms_phase", c_double * 8), ("residual_rel", c_double),
+                ("target_cells", c_int64), ("source_blocks", c_int64), ("target_blocks", c_int64),
+                ("pairs", c_int64), ("scratch_bytes", c_int64), ("kernel_launches", c_int64),
+                ("mac_mode_used", c_int32), ("reserved", c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("ms_phase", "reserved")}
+        d["ms_phase"] = {p: self.ms_phase[i] for i, p in enumerate(PHASES)}
+        return d
+
+
+_LIB = None
+
+
+def load():
+    """Load the in-tree ``liblgf.so``; raise if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2010_13213_gb300.build`"
+                               " (the CUDA path has no fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        lib.lgf_table_create.argtypes = [POINTER(c_void_p), c_int32, POINTER(c_int32), c_uint32, c_void_p]
+        lib.lgf_table_destroy.argtypes = [c_void_p]
+        lib.lgf_table_lgf_values.argtypes = [c_void_p, c_int32, POINTER(c_double)]
+        lib.lgf_poisson_solve.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p, c_int32,
+                                          POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
+        lib.lgf_heat_apply.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p, c_int32,
+                                       c_double, POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
+        lib.lgf_last_error.restype = c_char_p
+        lib.lgf_version.restype = c_char_p
+        for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
+                     "lgf_heat_apply"):
+            getattr(lib, name).restype = c_int32
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int):
+    if status != LGF_OK:
+        raise LgfError(status, lgf_last_error())
+
+
+def lgf_last_error() -> str:
+    return load().lgf_last_error().decode()
+
+
+def lgf_version() -> str:
+    return load().lgf_version().decode()
+
+
+class Mesh:
+    """Owns the host arrays behind an ``lgf_mesh`` (they must outlive the C call)."""
+
+    def __init__(self, levels, block: int, h0: float, n_ext: int = 16, roles=None):
+        self.levels = [np.ascontiguousarray(np.asarray(b, dtype=np.int32).reshape(-1, 3)) for b in levels]
+        self.nb = np.array([len(b) for b in self.levels], dtype=np.int32)
+        self.ijk = np.ascontiguousarray(np.concatenate(self.levels), dtype=np.int32)
+        self.roles = None if roles is None else np.ascontiguousarray(roles, dtype=np.uint8)
+        self.block, self.h0, self.n_ext = int(block), float(h0), int(n_ext)
+        self.c = lgf_mesh(len(self.levels), self.block, self.h0,
+                          self.nb.ctypes.data_as(POINTER(c_int32)), self.ijk.ctypes.data_as(POINTER(c_int32)),
+                          None if self.roles is None else self.roles.ctypes.data_as(POINTER(c_uint8)),
+                          self.n_ext)
+
+    @property
+    def total_blocks(self) -> int:
+        return int(self.nb.sum())
+
+
+def lgf_table_create(block: int, max_block_offset, flags: int = LGF_TBL_FP64, cuda_stream: int = 0):
+    """Returns the opaque table handle (an int)."""
+    h = c_void_p()
+    mo = (c_int32 * 3)(*[int(v) for v in max_block_offset])
+    _check(load().lgf_table_create(ctypes.byref(h), int(block), mo, int(flags), c_void_p(cuda_stream or None)))
+    return h.value
+
+
+def lgf_table_destroy(table) -> None:
+    _check(load().lgf_table_destroy(c_void_p(table)))
+
+
+def lgf_table_lgf_values(table, n: int) -> np.ndarray:
+    out = np.zeros((n + 1) ** 3)
+    _check(load().lgf_table_lgf_values(c_void_p(table), int(n), out.ctypes.data_as(POINTER(c_double))))
+    return out.reshape(n + 1, n + 1, n + 1)
+
+
+def _opts(precision=LGF_PREC_FP64, mac_mode=LGF_MAC_AUTO, residual=0, timing=0, residual_tol=0.0):
+    return lgf_solve_opts(int(precision), int(mac_mode), int(residual), int(timing), float(residual_tol))
+
+
+def lgf_poisson_solve(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, dtype: int = LGF_F64,
+                      opts: lgf_solve_opts | None = None, report: lgf_report | None = None,
+                      cuda_stream: int = 0) -> None:
+    _check(load().lgf_poisson_solve(c_void_p(table), ctypes.byref(mesh.c), int(ncomp), c_void_p(f_dev),
+                                    c_void_p(phi_dev), int(dtype),
+                                    ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(report) if report is not None else None,
+                                    c_void_p(cuda_stream or None)))
+
+
+def lgf_heat_apply(table, mesh: Mesh, ncomp: int, f_dev: int, g_dev: int, dtype: int, alpha_finest: float,
+                   opts: lgf_solve_opts | None = None, report: lgf_report | None = None,
+                   cuda_stream: int = 0) -> None:
+    _check(load().lgf_heat_apply(c_void_p(table or None), ctypes.byref(mesh.c), int(ncomp), c_void_p(f_dev),
+                                 c_void_p(g_dev), int(dtype), float(alpha_finest),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(report) if report is not None else None,
+                                 c_void_p(cuda_stream or None)))
+
+
+make_opts = _opts
