@@ -1,0 +1,292 @@
+"""Benchmark of the free-space LGF Poisson solve on one GB300 (replicas when --gpus N > 1).
+
+Workload (the headline configuration): single-level vector Poisson (3 components) for the
+streamfunction of a Gaussian-core vortex ring, R = 1, sigma = 0.2 R, h = R/32, 96x96x48 cells in
+16^3 blocks (108 blocks; source blocks are those with max|omega| >= 1e-6 max, all 108 here).
+A step is one complete ``lgf_poisson_solve`` (forward block transforms, per-frequency block-pair sum,
+inverse transforms) with inputs resident in HBM; the one-off LGF table is built before timing.
+
+Reported: Mcells/s of the mixed (double-float, DF32) path, whose error against the FP64 CPU oracle
+is checked outside the timed region (<= 1e-10 relative L-infinity), next to the FP64 path; the
+roofline of the dominant kernel; the CPU oracle (zero-padded FP64 FFT convolution) on the host
+cores; and an end-to-end number through the C ABI with host buffers.
+
+``--impl reference`` times the CPU oracle itself (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson-solve Mcells/s, mixed vs FP64 at rel err ≤1e-10; % of HBM roofline"
+WORKLOAD = "vortex-ring vector Poisson, R=1, sigma=0.2R, h=R/32, 96x96x48 cells, 16^3 blocks, 3 comps"
+FP32_INST_PEAK = 152 * 128 * 2.070e9  # FP32 lanes x SMs x max SM clock (instructions/s)
+FP64_FLOP_PEAK = 1.25e12              # nominal dense FP64 of GB300
+DF_OPS_PER_CMAC = 72                  # FP32 instructions of one double-float complex multiply-add
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_case():
+    import lgf_synth as S
+    case = S.single_level_ring()
+    src = {tuple(b) for b in case["src_blocks"]}
+    roles = np.array([2 + (1 if tuple(b) in src else 0) for b in case["blocks"]], np.uint8)
+    return case, roles
+
+
+def cpu_oracle_step(case):
+    """The oracle's FFT convolution of the full workload (FP64, host cores)."""
+    import oracle
+    return oracle.solve_box_fft(case["box"], case["h"])
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    import oracle
+    case, _ = build_case()
+    cells = int(np.prod(case["shape"]))
+    for _ in range(args.warmup):
+        cpu_oracle_step(case)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_step(case)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = cells / dt / 1e6
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mcells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "ncomp": 3},
+            "cpu_baseline": {"value": val, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+                             "sample": "full workload: zero-padded FP64 FFT convolution (scipy/numpy pocketfft)",
+                             "threads_used": oracle.num_threads()},
+            "e2e": {"value": val, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2010_13213_gb300.lgf as L
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case, roles = build_case()
+    B = case["B"]
+    cells = int(np.prod(case["shape"]))
+    ncomp = 3
+    mesh = L.Mesh([case["blocks"]], B, case["h"], roles=roles)
+    t_tab = time.perf_counter()
+    table = L.lgf_table_create(B, (5, 5, 2), L.LGF_TBL_FP64 | L.LGF_TBL_DF32 | L.LGF_TBL_FP32)
+    t_tab = time.perf_counter() - t_tab
+    f = torch.from_numpy(case["f"]).to(dev)
+    phi = torch.zeros_like(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def solve(prec, rep=None, timing=0, fin=f, fout=phi):
+        L.lgf_poisson_solve(table, mesh, ncomp, fin.data_ptr(), fout.data_ptr(), L.LGF_F64,
+                            L.make_opts(precision=prec, mac_mode=L.LGF_MAC_PAIR, timing=timing), rep, stream)
+
+    # accuracy outside the timed region: against the oracle (rank 0 computes, all ranks check)
+    ref = cpu_oracle_step(case)
+    import lgf_synth as S
+    errs = {}
+    for name, prec in (("fp64", L.LGF_PREC_FP64), ("df32", L.LGF_PREC_DF32), ("fp32", L.LGF_PREC_FP32)):
+        solve(prec)
+        torch.cuda.synchronize()
+        got = S.blocks_to_box(phi.cpu().numpy(), case["blocks"], B, case["shape"])
+        errs[name] = float(max(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max() for c in range(2)))
+
+    def timed(prec):
+        for _ in range(args.warmup):
+            solve(prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        step_ms, mac_ms = [], []
+        rep = L.lgf_report()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # L2 flush between timed steps (256 MiB write), outside the events
+            solve(prec, rep, timing=1)
+            step_ms.append(rep.ms_total)
+            mac_ms.append(rep.ms_phase[3])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        return float(np.mean(step_ms)), float(np.mean(mac_ms)), wall, rep
+
+    with ClockSampler(local) as clk:
+        ms_df, mac_df, wall_df, rep_df = timed(L.LGF_PREC_DF32)
+        ms_64, mac_64, wall_64, rep_64 = timed(L.LGF_PREC_FP64)
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    h_in = torch.from_numpy(case["f"]).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(f)
+    d_out = torch.empty_like(f)
+    for _ in range(args.warmup):
+        d_in.copy_(h_in, non_blocking=True)
+        solve(L.LGF_PREC_DF32, fin=d_in, fout=d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        d_in.copy_(h_in, non_blocking=True)
+        solve(L.LGF_PREC_DF32, fin=d_in, fout=d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # max over ranks
+    vals = torch.tensor([ms_df, ms_64, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_df, ms_64, e2e_ms = vals.tolist()
+    L.lgf_table_destroy(table)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    W = (2 * B) ** 2 * (B + 1)
+    pairs = rep_df.pairs
+    cmacs = pairs * W * ncomp
+    ach_df = cmacs * DF_OPS_PER_CMAC / (mac_df * 1e-3)
+    roof = {"kernel": "k_mac_pair<df> (block-pair multiply-accumulate)", "bound": "alu",
+            "achieved": ach_df / 1e12, "peak": FP32_INST_PEAK / 1e12, "unit": "T FP32-inst/s",
+            "frac": ach_df / FP32_INST_PEAK, "traffic": None,
+            "note": f"{DF_OPS_PER_CMAC} FP32 instructions per double-float complex MAC x {cmacs:.3e} MACs;"
+                    " peak = 152 SMs x 128 lanes x 2070 MHz (derived)"}
+    cores = os.cpu_count()
+    t0 = time.perf_counter()
+    cpu_oracle_step(case)
+    cpu_dt = time.perf_counter() - t0
+    import oracle
+    line = {
+        "metric": METRIC, "value": cells * world / (ms_df * 1e-3) / 1e6, "unit": "Mcells/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_df,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": cells, "ncomp": ncomp, "blocks": int(len(case["blocks"])),
+                   "mac_mode": "pair", "parallelism": f"replicas{world}",
+                   "l2": "flushed by a 256 MiB write between timed steps (outside the step events)"},
+        "rel_err": errs,
+        "fp64": {"value": cells * world / (ms_64 * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": ms_64,
+                 "mac_ms": mac_64,
+                 "mac_frac_fp64_peak": pairs * W * ncomp * 8 / (mac_64 * 1e-3) / FP64_FLOP_PEAK},
+        "phases_ms_df32": {k: v for k, v in L.lgf_report.as_dict(rep_df)["ms_phase"].items() if v},
+        "table_build_s": t_tab,
+        "roofline": roof,
+        "cpu_baseline": {"value": cells / cpu_dt / 1e6, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+                         "sample": "full workload once: zero-padded FP64 FFT convolution (pocketfft)",
+                         "threads_used": oracle.num_threads()},
+        "e2e": {"value": cells * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s",
+                "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)},
+        "gpu_launches": int(rep_df.kernel_launches) * args.steps,
+        "clocks": clocks,
+        "wall_s_timed": {"df32": wall_df, "fp64": wall_64},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
