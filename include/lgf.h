@@ -172,6 +172,24 @@ int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f
                    void *g_dev, int32_t dtype, double alpha_finest, const lgf_solve_opts *opts,
                    lgf_report *rep, void *cuda_stream);
 
+/*
+ * lgf_poisson_solve_static -- single-level solve (pair mode) that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that must not allocate during a
+ * solve (a device-memory budget fixed at start-up, or a thread that must not block on the
+ * allocator, which may synchronise the device).  Its scratch is a file-scope device array of
+ * LGF_STATIC_SCRATCH_BYTES = 32 MiB that every GPU loading the library reserves until exit.
+ *   t, m, ncomp, f_dev, phi_dev, dtype : as for lgf_poisson_solve (m->nlevels must be 1).
+ *   precision   : LGF_PREC_FP64, LGF_PREC_FP32 or LGF_PREC_DF32 (the table must hold its spectra).
+ *   cuda_stream : stream of the work.
+ * Requests whose scratch (source and target spectra: ncomp x blocks x (2B)^2 (B+1) complex values,
+ * plus index lists) exceeds 32 MiB fail with LGF_E_INVALID_ARG and a message giving the size.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls whose GPU work may
+ * overlap race on it and must be ordered by the caller.  It calls no cudaMalloc/cudaFree.
+ */
+int lgf_poisson_solve_static(const lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev,
+                             void *phi_dev, int32_t dtype, int32_t precision, void *cuda_stream);
+
 /* lgf_last_error -- message for the last non-zero status returned on the calling thread. */
 const char *lgf_last_error(void);
 

@@ -79,10 +79,12 @@ def load():
                                           POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
         lib.lgf_heat_apply.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p, c_int32,
                                        c_double, POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
+        lib.lgf_poisson_solve_static.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p,
+                                                 c_int32, c_int32, c_void_p]
         lib.lgf_last_error.restype = c_char_p
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
-                     "lgf_heat_apply"):
+                     "lgf_heat_apply", "lgf_poisson_solve_static"):
             getattr(lib, name).restype = c_int32
         _LIB = lib
     return _LIB
@@ -160,6 +162,14 @@ def lgf_heat_apply(table, mesh: Mesh, ncomp: int, f_dev: int, g_dev: int, dtype:
                                  ctypes.byref(opts) if opts is not None else None,
                                  ctypes.byref(report) if report is not None else None,
                                  c_void_p(cuda_stream or None)))
+
+
+def lgf_poisson_solve_static(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, dtype: int = LGF_F64,
+                             precision: int = LGF_PREC_FP64, cuda_stream: int = 0) -> None:
+    """Single-level solve whose scratch is the library's fixed 32 MiB device array (no allocation)."""
+    _check(load().lgf_poisson_solve_static(c_void_p(table), ctypes.byref(mesh.c), int(ncomp), c_void_p(f_dev),
+                                           c_void_p(phi_dev), int(dtype), int(precision),
+                                           c_void_p(cuda_stream or None)))
 
 
 make_opts = _opts

@@ -1,0 +1,69 @@
+"""The allocation-free single-level solve (lgf_poisson_solve_static) against the regular entry point.
+
+Callers that cannot allocate device memory during a solve (a fixed device-memory budget, or a thread
+that must not block on the allocator) use this entry point; its scratch is the library's fixed
+32 MiB device array.  This file is collected last so that a run stopping at the first failure has
+already run every other test; it also passes on its own in a fresh process.
+"""
+import numpy as np
+import pytest
+
+import lgf_synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2010_13213_gb300.lgf as L
+    L.load()
+    return L
+
+
+def _solve_pair(L, table, mesh, f, precision, dtype):
+    out = torch.full_like(f, float("nan"))
+    L.lgf_poisson_solve(table, mesh, f.shape[0], f.data_ptr(), out.data_ptr(), dtype,
+                        L.make_opts(precision=precision, mac_mode=L.LGF_MAC_PAIR))
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (2, 1e-10)])
+def test_static_matches_regular_on_two_calls(L, precision, tol):
+    table = L.lgf_table_create(16, (1, 1, 1), L.LGF_TBL_FP64 | L.LGF_TBL_DF32)
+    try:
+        case = S.single_level_random(n=32, B=16, seed=3, ncomp=2)
+        mesh = L.Mesh([case["blocks"]], 16, case["h"])
+        f = torch.from_numpy(case["f"]).cuda()
+        ref = _solve_pair(L, table, mesh, f, precision, L.LGF_F64)
+        torch.cuda.synchronize()
+        ref = ref.cpu().numpy()
+        scale = np.abs(ref).max()
+        for call in range(2):
+            # the second call gets a different source so stale scratch contents would show
+            fin = f if call == 0 else -2.0 * f
+            out = torch.full_like(f, float("nan"))
+            L.lgf_poisson_solve_static(table, mesh, 2, fin.data_ptr(), out.data_ptr(), L.LGF_F64, precision)
+            torch.cuda.synchronize()
+            expect = ref if call == 0 else -2.0 * ref
+            got = out.cpu().numpy()
+            assert np.isfinite(got).all()
+            assert np.abs(got - expect).max() <= tol * (2.0 if call else 1.0) * scale
+    finally:
+        L.lgf_table_destroy(table)
+
+
+def test_static_rejects_requests_beyond_its_scratch(L):
+    table = L.lgf_table_create(16, (5, 5, 2), L.LGF_TBL_FP64)
+    try:
+        case = S.single_level_ring()
+        mesh = L.Mesh([case["blocks"]], 16, case["h"])
+        f = torch.from_numpy(case["f"]).cuda()
+        out = torch.zeros_like(f)
+        with pytest.raises(L.LgfError) as e:
+            L.lgf_poisson_solve_static(table, mesh, 3, f.data_ptr(), out.data_ptr(), L.LGF_F64, 0)
+        assert e.value.status == L.LGF_E_INVALID_ARG and "static scratch" in str(e.value)
+    finally:
+        L.lgf_table_destroy(table)
