@@ -1,0 +1,285 @@
+// amr.cuh -- stencil kernels of the composite-mesh path (Sec. 3.2-3.5), templated on the arithmetic.
+//
+//   k_restrict   F_k = [Omega_k] fhat_k + [covered] mean of the 8 children of F_{k+1}
+//                (cumulative coarsening, step 1 of FLGF-AMR)
+//   k_interp     c_k = P_{k-1->k} psi_{k-1}: cell-centred tensor-product linear interpolation
+//   k_correct    A_k = [Omega_k] fhat_k + [Omega_k u Omega_k^E] (P L_{k-1} psi_{k-1} - L_k c_k)
+//                (the commutation source correction S psi_{k-1}, Eq. (eq:source_correct))
+//   k_residual   FP64 max |L_k phi^k - F_k - P L_{k-1} psi_{k-1}| over interior Omega_k cells
+//   k_heat_*     FIF-AMR: P_k fhat and the separable discrete heat kernel (Sec. 3.5)
+// Fields are stored per level as [ncomp][nBL][B^3] over the level's internal block set; a dense
+// block map (block coords -> index, -1 if absent) gives neighbours across block boundaries.
+#pragma once
+#include "common.cuh"
+
+struct LevelDev {
+  const int32_t *map;      // [n.z][n.y][n.x] block map
+  int3 lo, n;              // block-coordinate box of the map
+  const uint8_t *cellmask; // [nBL][B^3] CellBits
+  const int32_t *user_of;  // [nBL] caller block index or -1
+  int shift;               // log2(B)
+  double h;                // level spacing
+};
+
+LGF_D int level_block(const LevelDev &L, int bx, int by, int bz) {
+  bx -= L.lo.x;
+  by -= L.lo.y;
+  bz -= L.lo.z;
+  if ((unsigned)bx >= (unsigned)L.n.x || (unsigned)by >= (unsigned)L.n.y || (unsigned)bz >= (unsigned)L.n.z)
+    return -1;
+  return L.map[((int64_t)bz * L.n.y + by) * L.n.x + bx];
+}
+
+// Cell (gx, gy, gz) of a level -> (block index, offset inside the block); false if absent.
+LGF_D bool level_cell(const LevelDev &L, int gx, int gy, int gz, int &blk, int &off) {
+  const int B = 1 << L.shift, m = B - 1;
+  blk = level_block(L, gx >> L.shift, gy >> L.shift, gz >> L.shift);
+  off = (((gz & m) << L.shift) + (gy & m)) * B + (gx & m);
+  return blk >= 0;
+}
+
+template <class R>
+LGF_D R nan_of() {
+  return RT<R>::from(__longlong_as_double(0x7ff8000000000000ll));
+}
+
+// value of an internal field (R storage) at a level cell; NaN when the block is absent
+template <class R>
+LGF_D R fetch(const LevelDev &L, const R *buf, int64_t cs, int comp, int gx, int gy, int gz) {
+  int blk, off;
+  if (!level_cell(L, gx, gy, gz, blk, off)) return nan_of<R>();
+  return buf[comp * cs + ((int64_t)blk << (3 * L.shift)) + off];
+}
+
+// 7-point Laplacian of an internal field at a level cell
+template <class R>
+LGF_D R lap7(const LevelDev &L, const R *buf, int64_t cs, int comp, int x, int y, int z, R inv_h2) {
+  R c = fetch<R>(L, buf, cs, comp, x, y, z);
+  R s = fetch<R>(L, buf, cs, comp, x + 1, y, z) + fetch<R>(L, buf, cs, comp, x - 1, y, z);
+  s = s + fetch<R>(L, buf, cs, comp, x, y + 1, z) + fetch<R>(L, buf, cs, comp, x, y - 1, z);
+  s = s + fetch<R>(L, buf, cs, comp, x, y, z + 1) + fetch<R>(L, buf, cs, comp, x, y, z - 1);
+  return (s - RT<R>::from(6.0) * c) * inv_h2;
+}
+
+// P_{k-1->k}: fine cell (fx, fy, fz) -> sum over the 8 coarse corners of prod (3/4 | 1/4) * value
+template <class R, class F>
+LGF_D R interp_at(int fx, int fy, int fz, F coarse_value) {
+  const int px = fx >> 1, py = fy >> 1, pz = fz >> 1;
+  const int qx = (fx & 1) ? px + 1 : px - 1;
+  const int qy = (fy & 1) ? py + 1 : py - 1;
+  const int qz = (fz & 1) ? pz + 1 : pz - 1;
+  const R w3 = RT<R>::from(0.75), w1 = RT<R>::from(0.25);
+  R acc = RT<R>::zero();
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cx = (c & 1) ? qx : px, cy = (c & 2) ? qy : py, cz = (c & 4) ? qz : pz;
+    const R w = ((c & 1) ? w1 : w3) * ((c & 2) ? w1 : w3) * ((c & 4) ? w1 : w3);
+    acc = acc + w * coarse_value(cx, cy, cz);
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------ restriction (step 1)
+// grid (nU_k, ncomp), 256 threads.  F_k on the caller blocks of level k (BL index = caller index).
+template <class R>
+__global__ void __launch_bounds__(256) k_restrict(LevelDev L, const void *f_user, int dtype, int64_t ucs,
+                                                  int64_t user_off, R *F, int64_t cs) {
+  const int b = blockIdx.x, comp = blockIdx.y, B3 = 1 << (3 * L.shift);
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    const uint8_t cm = L.cellmask[(int64_t)b * B3 + off];
+    R v = RT<R>::zero();
+    if (cm & 1) v = load_field<R>(f_user, comp * ucs + (user_off + b) * (int64_t)B3 + off, dtype);
+    F[comp * cs + (int64_t)b * B3 + off] = v;
+  }
+}
+
+// coarsening part: for covered cells, F_k += mean of children.  One thread per level-(k+1) caller
+// cell group: each fine caller block covers one octant of its parent; grid (nU_{k+1}, ncomp).
+template <class R>
+__global__ void __launch_bounds__(256) k_coarsen_add(LevelDev Lc, R *Fc, int64_t ccs, const int4 *fine_blocks,
+                                                     const R *Ff, int64_t fcs) {
+  const int fb = blockIdx.x, comp = blockIdx.y, sh = Lc.shift, B = 1 << sh, H = B >> 1;
+  const int4 c = fine_blocks[fb];
+  const int B3 = B * B * B;
+  for (int t = threadIdx.x; t < H * H * H; t += blockDim.x) {
+    const int x = t % H, y = (t / H) % H, z = t / (H * H);
+    // coarse cell = (B c + 2 (x, y, z)) / 2
+    const int gx = (c.x << (sh - 1)) + x, gy = (c.y << (sh - 1)) + y, gz = (c.z << (sh - 1)) + z;
+    R s = RT<R>::zero();
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int lx = 2 * x + (d & 1), ly = 2 * y + ((d >> 1) & 1), lz = 2 * z + ((d >> 2) & 1);
+      s = s + Ff[comp * fcs + (int64_t)fb * B3 + (lz * B + ly) * B + lx];
+    }
+    int blk, off;
+    if (level_cell(Lc, gx, gy, gz, blk, off)) {
+      R &d = Fc[comp * ccs + (int64_t)blk * B3 + off];
+      d = d + RT<R>::from(0.125) * s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ interpolation c_k = P psi_{k-1}
+// grid (nBL_k, ncomp)
+template <class R>
+__global__ void __launch_bounds__(256) k_interp(LevelDev L, const int4 *blocks, R *c, int64_t cs, LevelDev Lc,
+                                                const R *psi, int64_t pcs) {
+  const int b = blockIdx.x, comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+  const int B3 = B * B * B;
+  const int4 bc = blocks[b];
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+              z = (bc.z << sh) + (off >> (2 * sh));
+    c[comp * cs + (int64_t)b * B3 + off] =
+        interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, psi, pcs, comp, i, j, k); });
+  }
+}
+
+// ------------------------------------------------------------------ correction source A_k
+// grid (|SA_k|, ncomp).  A[b] for b = SA[i].  k = 0: A = [OM] fhat.
+template <class R>
+__global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks, const int32_t *SA,
+                                                 const void *f_user, int dtype, int64_t ucs, R *A, int64_t cs,
+                                                 const R *c, LevelDev Lc, const R *psi, int64_t pcs,
+                                                 int has_coarse) {
+  const int b = SA[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+  const int B3 = B * B * B;
+  const int4 bc = blocks[b];
+  const int u = L.user_of[b];
+  const R inv_h2f = RT<R>::from(1.0 / (L.h * L.h));
+  const R inv_h2c = RT<R>::from(1.0 / (Lc.h * Lc.h));
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    const uint8_t cm = L.cellmask[(int64_t)b * B3 + off];
+    R v = RT<R>::zero();
+    if ((cm & 1) && u >= 0) v = load_field<R>(f_user, comp * ucs + (int64_t)u * B3 + off, dtype);
+    if (has_coarse && (cm & 3)) {
+      const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+                z = (bc.z << sh) + (off >> (2 * sh));
+      const R plp = interp_at<R>(
+          x, y, z, [&](int i, int j, int k) { return lap7<R>(Lc, psi, pcs, comp, i, j, k, inv_h2c); });
+      const R lpc = lap7<R>(L, c, cs, comp, x, y, z, inv_h2f);
+      v = v + (plp - lpc);
+    }
+    A[comp * cs + (int64_t)b * B3 + off] = v;
+  }
+}
+
+// ------------------------------------------------------------------ FP64 residual
+// grid (|Tphi_k|, ncomp).  r = L_k phi - F_k - [k >= 1] P L_{k-1} psi_{k-1} at Omega_k cells whose six
+// neighbours are Omega_k cells; out[0] = max |r|, out[1] = max |F + P L psi| (as ordered uint64 bits).
+template <class R>
+__global__ void __launch_bounds__(256) k_residual(LevelDev L, const int4 *blocks, const int32_t *Tphi,
+                                                  const void *phi_user, int dtype, int64_t ucs, const R *F,
+                                                  int64_t cs, LevelDev Lc, const R *psi, int64_t pcs,
+                                                  int has_coarse, unsigned long long *out) {
+  const int b = Tphi[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+  const int B3 = B * B * B;
+  const int4 bc = blocks[b];
+  const double inv_h2f = 1.0 / (L.h * L.h), inv_h2c = 1.0 / (Lc.h * Lc.h);
+  double rmax = 0.0, smax = 0.0;
+  auto phi_at = [&](int x, int y, int z, bool &ok) -> double {
+    int blk, off;
+    if (!level_cell(L, x, y, z, blk, off)) {
+      ok = false;
+      return 0.0;
+    }
+    if (!(L.cellmask[(int64_t)blk * B3 + off] & 1)) ok = false;
+    const int uu = L.user_of[blk];
+    if (uu < 0) {
+      ok = false;
+      return 0.0;
+    }
+    return load_field<double>(phi_user, comp * ucs + (int64_t)uu * B3 + off, dtype);
+  };
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    if (!(L.cellmask[(int64_t)b * B3 + off] & 1)) continue;
+    const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+              z = (bc.z << sh) + (off >> (2 * sh));
+    bool ok = true;
+    const double c0 = phi_at(x, y, z, ok);
+    double s = phi_at(x + 1, y, z, ok) + phi_at(x - 1, y, z, ok) + phi_at(x, y + 1, z, ok) +
+               phi_at(x, y - 1, z, ok) + phi_at(x, y, z + 1, ok) + phi_at(x, y, z - 1, ok);
+    if (!ok) continue;
+    double src = RT<R>::to_d(F[comp * cs + (int64_t)b * B3 + off]);
+    if (has_coarse) {
+      src += interp_at<double>(x, y, z, [&](int i, int j, int k) {
+        return RT<R>::to_d(lap7<R>(Lc, psi, pcs, comp, i, j, k, RT<R>::from(inv_h2c)));
+      });
+    }
+    const double ar = fabs((s - 6.0 * c0) * inv_h2f - src);
+    rmax = (ar != ar) ? 1e300 : fmax(rmax, ar);
+    smax = fmax(smax, fabs(src));
+  }
+  // block reduce via atomics on the ordered bit patterns of non-negative doubles
+  if (rmax > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(rmax));
+  if (smax > 0.0) atomicMax(out + 1, (unsigned long long)__double_as_longlong(smax));
+}
+
+// ------------------------------------------------------------------ heat apply (FIF-AMR)
+struct HeatW {
+  double w[65];  // w[n] = e^{-2 alpha} I_n(2 alpha), n <= r
+  int r;
+};
+
+// U_k = [OM] fhat_k + P U_{k-1} (k >= 1), or S_k = F_k + P U_{k-1}; grid (|HB_k|, ncomp).
+// mode 0: out = [OM] fhat (+ P U_{k-1});  mode 1: out = F (+ P U_{k-1})
+template <class R>
+__global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *blocks, const int32_t *HB, int mode,
+                                                    const void *f_user, int dtype, int64_t ucs, const R *F,
+                                                    int nU, R *out, int64_t cs, LevelDev Lc, const R *Uc,
+                                                    int64_t ucs_c, int has_coarse) {
+  const int b = HB[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+  const int B3 = B * B * B;
+  const int4 bc = blocks[b];
+  const int u = L.user_of[b];
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    R v = RT<R>::zero();
+    if (mode == 0) {
+      if ((L.cellmask[(int64_t)b * B3 + off] & 1) && u >= 0)
+        v = load_field<R>(f_user, comp * ucs + (int64_t)u * B3 + off, dtype);
+    } else if (b < nU) {
+      v = F[comp * cs + (int64_t)b * B3 + off];
+    }
+    if (has_coarse) {
+      const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+                z = (bc.z << sh) + (off >> (2 * sh));
+      v = v + interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, Uc, ucs_c, comp, i, j, k); });
+    }
+    out[comp * cs + (int64_t)b * B3 + off] = v;
+  }
+}
+
+// One separable pass of E_alpha along `axis` over the heat block set; absent neighbours read 0.
+template <class R>
+__global__ void __launch_bounds__(256) k_heat_pass(LevelDev L, const int4 *blocks, const int32_t *HB, int axis,
+                                                   const R *in, R *out, int64_t cs, HeatW w) {
+  const int b = HB[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+  const int B3 = B * B * B;
+  const int4 bc = blocks[b];
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+              z = (bc.z << sh) + (off >> (2 * sh));
+    R acc = RT<R>::from(w.w[0]) * in[comp * cs + (int64_t)b * B3 + off];
+    for (int d = 1; d <= w.r; ++d) {
+      const R wd = RT<R>::from(w.w[d]);
+      int blk, o2;
+      R s = RT<R>::zero();
+      const int dx = axis == 0 ? d : 0, dy = axis == 1 ? d : 0, dz = axis == 2 ? d : 0;
+      if (level_cell(L, x + dx, y + dy, z + dz, blk, o2)) s = s + in[comp * cs + (int64_t)blk * B3 + o2];
+      if (level_cell(L, x - dx, y - dy, z - dz, blk, o2)) s = s + in[comp * cs + (int64_t)blk * B3 + o2];
+      acc = acc + wd * s;
+    }
+    out[comp * cs + (int64_t)b * B3 + off] = acc;
+  }
+}
+
+// g_user on Omega_k cells of the caller blocks; grid (nU_k, ncomp)
+template <class R>
+__global__ void __launch_bounds__(256) k_heat_store(LevelDev L, const R *g, int64_t cs, void *g_user, int dtype,
+                                                    int64_t ucs, int64_t user_off) {
+  const int b = blockIdx.x, comp = blockIdx.y, B3 = 1 << (3 * L.shift);
+  for (int off = threadIdx.x; off < B3; off += blockDim.x)
+    if (L.cellmask[(int64_t)b * B3 + off] & 1)
+      store_field<R>(g_user, comp * ucs + (user_off + b) * (int64_t)B3 + off, dtype,
+                     g[comp * cs + (int64_t)b * B3 + off]);
+}

@@ -25,7 +25,23 @@ int set_error(int code, const char *fmt, ...) {
   return code;
 }
 
+// Workspaces are per (table, stream); calls without a table (heat apply) share a process-wide map
+// keyed by (device, stream).
+static std::mutex g_ws_mu;
+static std::map<std::pair<int, void *>, Workspace *> g_ws;
+
 Workspace *workspace_for(lgf_table *t, cudaStream_t st) {
+  if (!t) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    auto key = std::make_pair(dev, (void *)st);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) return it->second;
+    Workspace *w = new Workspace();
+    g_ws[key] = w;
+    return w;
+  }
   std::lock_guard<std::mutex> g(t->mu);
   auto it = t->ws.find((void *)st);
   if (it != t->ws.end()) return it->second;

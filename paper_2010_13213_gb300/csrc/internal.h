@@ -72,13 +72,18 @@ int build_spectra(int B, const double *Gd, int K, int3 mo, int noff, void *s64, 
 // pair_*.cu: launch wrappers, one instantiation per arithmetic
 template <class R>
 struct PairOps {
-  static int forward(int B, const void *f, int dtype, int64_t comp_stride, const int32_t *src_idx,
-                     int nsrc, int ncomp, void *spec, cudaStream_t st);
-  static int inverse(int B, const void *spec, int ntgt, int ncomp, const int32_t *tgt_idx, void *out,
-                     int dtype, int64_t comp_stride, const void *addend, int add_dtype, double scale,
-                     cudaStream_t st);
-  static int mac(int B, const void *F, int nsrc, const int4 *src_c, const void *Gh, int3 mo,
-                 void *Phi, int ntgt, const int4 *tgt_c, int ncomp, int accumulate, cudaStream_t st);
+  // spectra of the zero-padded blocks src_idx[i] of f ([ncomp][*][B^3], dtype code of load_field),
+  // cells masked by cellmask & bits when cellmask != null; out [ncomp][nsrc][W]
+  static int forward(int B, const void *f, int dtype, int64_t comp_stride, const int32_t *src_idx, int nsrc,
+                     int ncomp, void *spec, const uint8_t *cellmask, int bits, cudaStream_t st);
+  // see k_block_inv
+  static int inverse(int B, const void *spec, int64_t spec_cs, const int32_t *rows, const int32_t *aux, int n,
+                     int ncomp, void *out, int dtype, int64_t out_cs, int64_t out_off, const void *addend,
+                     int64_t add_cs, const uint8_t *cellmask, int bits, double scale, cudaStream_t st);
+  // see k_mac_pair; strides in complex elements
+  static int mac(int B, const void *F, int nsrc, int64_t f_cs, const int32_t *src_list, const int4 *src_coords,
+                 const void *Gh, int3 mo, void *Phi, int ntgt, int64_t p_cs, const int32_t *tgt_list,
+                 const int4 *tgt_coords, int ncomp, int accumulate, cudaStream_t st);
 };
 
 // Growable device buffer (never shrinks; freed with the owner).

@@ -1,0 +1,447 @@
+// multi.cu -- host drivers of the composite-mesh Poisson solve (FLGF-AMR, Sec. 3.4) and of the
+// heat apply (FIF-AMR, Sec. 3.5), plus the plan cache.
+//
+// FLGF-AMR, per call:
+//   1. fine to coarse:  F_k = [Omega_k] fhat_k + P_{k+1->k} F_{k+1}            (k_restrict, k_coarsen_add)
+//   2. coarse to fine, level k:
+//        c_k   = P_{k-1->k} psi_{k-1}                                          (k_interp, k >= 1)
+//        A_k   = [Omega_k] fhat_k + [Omega_k u Omega_k^E] S psi_{k-1}           (k_correct)
+//        Fhat  = spectra of A_k (blocks SA) and of F_k on covered cells (blocks SB) (k_block_fwd)
+//        Phi   = sum over pairs of Ghat * Fhat_A for all targets                (k_mac_pair)
+//        psi_k = c_k + h_k^2 G * A_k on the psi targets                         (k_block_inv)
+//        Phi  += sum over pairs of Ghat * Fhat_B on the Omega_k targets          (k_mac_pair)
+//        phi   = c_k + h_k^2 G * (A_k + B_k) written on Omega_k                  (k_block_inv)
+//   3. optional FP64 residual L_k phi - F_k - P L_{k-1} psi_{k-1}                (k_residual)
+#include <string.h>
+
+#include <algorithm>
+#include <list>
+#include <string>
+#include <vector>
+
+#include "amr.cuh"
+#include "plan.h"
+#include "solver.h"
+
+namespace lgf {
+
+// ------------------------------------------------------------------ plan cache (process-wide)
+static std::mutex g_plan_mu;
+static std::list<std::pair<std::string, Plan *>> g_plans;  // most recent first
+
+static std::string plan_key(const lgf_mesh *m, const int *radii) {
+  std::string k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int64_t tot = 0;
+  for (int i = 0; i < m->nlevels; ++i) tot += m->nblocks[i];
+  auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
+  put(&dev, sizeof dev);
+  put(&m->nlevels, 4);
+  put(&m->block, 4);
+  put(&m->n_ext, 4);
+  put(m->nblocks, 4 * (size_t)m->nlevels);
+  put(m->block_ijk, 12 * (size_t)tot);
+  const char h = radii ? 1 : 0;
+  put(&h, 1);
+  if (radii) put(radii, 4 * (size_t)m->nlevels);
+  return k;
+}
+
+int get_plan(const lgf_mesh *m, const int *radii, Plan **out) {
+  const std::string key = plan_key(m, radii);
+  std::lock_guard<std::mutex> g(g_plan_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end(); ++it)
+    if (it->first == key) {
+      g_plans.splice(g_plans.begin(), g_plans, it);
+      *out = it->second;
+      return LGF_OK;
+    }
+  Plan *P = nullptr;
+  int rc = build_plan(m, radii, &P);
+  if (rc) return rc;
+  g_plans.emplace_front(key, P);
+  while (g_plans.size() > 32) {
+    delete g_plans.back().second;  // cudaFree inside orders against in-flight work
+    g_plans.pop_back();
+  }
+  *out = P;
+  return LGF_OK;
+}
+
+static LevelDev level_dev(const Plan *P, int k) {
+  const LevelPlan &L = P->L[k];
+  LevelDev d;
+  d.map = L.d_map;
+  d.lo = make_int3(L.bb_lo[0], L.bb_lo[1], L.bb_lo[2]);
+  d.n = make_int3(L.bb_n[0], L.bb_n[1], L.bb_n[2]);
+  d.cellmask = L.d_cellmask;
+  d.user_of = L.d_user_of;
+  int s = 0;
+  while ((1 << s) < P->B) ++s;
+  d.shift = s;
+  d.h = L.h;
+  return d;
+}
+
+template <class R>
+static const void *spectra_for(const lgf_table *t);
+template <>
+const void *spectra_for<double>(const lgf_table *t) { return t->s64; }
+template <>
+const void *spectra_for<float>(const lgf_table *t) { return t->s32; }
+template <>
+const void *spectra_for<df>(const lgf_table *t) { return t->sdf; }
+
+static int check_range(const Plan *P, const lgf_table *t) {
+  const int mo[3] = {t->mo.x, t->mo.y, t->mo.z};
+  for (const auto &L : P->L) {
+    int slo[3] = {1 << 30, 1 << 30, 1 << 30}, shi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    int tlo[3] = {1 << 30, 1 << 30, 1 << 30}, thi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    auto acc = [&](const std::vector<int32_t> &lst, int *lo, int *hi) {
+      for (int b : lst) {
+        const int v[3] = {L.BL[b].x, L.BL[b].y, L.BL[b].z};
+        for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], v[a]), hi[a] = std::max(hi[a], v[a]);
+      }
+    };
+    acc(L.SA, slo, shi);
+    acc(L.SB, slo, shi);
+    acc(L.Tall, tlo, thi);
+    if (L.Tall.empty() || (L.SA.empty() && L.SB.empty())) continue;
+    for (int a = 0; a < 3; ++a) {
+      const int reach = std::max(thi[a] - slo[a], shi[a] - tlo[a]);
+      if (reach > mo[a])
+        return set_error(LGF_E_TABLE_RANGE,
+                         "level %d needs block offsets up to %d along axis %d; the table covers %d", L.k, reach,
+                         a, mo[a]);
+    }
+  }
+  return LGF_OK;
+}
+
+#define LGF_LAUNCH_CHECK(what)                                                                   \
+  do {                                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                         \
+    if (e_ != cudaSuccess) return set_error(LGF_E_CUDA, "%s launch: %s", what, cudaGetErrorString(e_)); \
+    ++launches;                                                                                  \
+  } while (0)
+
+template <class R>
+static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
+                         const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  Plan *P = nullptr;
+  int rc = get_plan(m, nullptr, &P);
+  if (rc) return rc;
+  if ((rc = check_range(P, t))) return rc;
+  const void *Gh = spectra_for<R>(t);
+  if (!Gh) return set_error(LGF_E_INVALID_ARG, "table lacks the spectra of the requested precision");
+  const int B = P->B, K = P->K;
+  const int64_t B3 = (int64_t)B * B * B;
+  const int W = (2 * B) * (2 * B) * (B + 1);
+  int64_t total_user = 0;
+  for (int k = 0; k < K; ++k) total_user += P->L[k].nU;
+  const int64_t ucs = total_user * B3;
+  // workspace layout
+  std::vector<int64_t> Foff(K + 1, 0), cs(K);
+  int64_t maxBL = 0, maxSA = 0, maxSB = 0, maxT = 0;
+  for (int k = 0; k < K; ++k) {
+    const LevelPlan &L = P->L[k];
+    cs[k] = (int64_t)L.BL.size() * B3;
+    Foff[k + 1] = Foff[k] + ncomp * cs[k];
+    maxBL = std::max<int64_t>(maxBL, (int64_t)L.BL.size());
+    maxSA = std::max<int64_t>(maxSA, (int64_t)L.SA.size());
+    maxSB = std::max<int64_t>(maxSB, (int64_t)L.SB.size());
+    maxT = std::max<int64_t>(maxT, (int64_t)L.nTall);
+  }
+  Workspace *ws = workspace_for(t, st);
+  const size_t field = sizeof(R) * (size_t)ncomp * maxBL * B3;
+  if ((rc = ws->buf[0].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxSA, 1) * W)) ||
+      (rc = ws->buf[1].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxT, 1) * W)) ||
+      (rc = ws->buf[3].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxSB, 1) * W)) ||
+      (rc = ws->buf[4].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[5].reserve(field)) ||
+      (rc = ws->buf[6].reserve(field)) || (rc = ws->buf[7].reserve(sizeof(R) * (size_t)Foff[K])) ||
+      (rc = ws->buf[9].reserve(sizeof(unsigned long long) * 2 * K)))
+    return rc;
+  cx<R> *FA = (cx<R> *)ws->buf[0].p, *Phi = (cx<R> *)ws->buf[1].p, *FB = (cx<R> *)ws->buf[3].p;
+  R *Fall = (R *)ws->buf[4].p, *A = (R *)ws->buf[5].p, *c = (R *)ws->buf[6].p;
+  R *Psi = (R *)ws->buf[7].p;  // psi_k of every level, [level][ncomp][nBL_k][B^3]
+  unsigned long long *racc = (unsigned long long *)ws->buf[9].p;
+  int64_t launches = 0;
+  PhaseTimer tm;
+  tm.start(o.timing != 0, st);
+  // 1. cumulative coarsening
+  for (int k = K - 1; k >= 0; --k) {
+    const LevelPlan &L = P->L[k];
+    const LevelDev Ld = level_dev(P, k);
+    k_restrict<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, f, dtype, ucs, L.user_off, Fall + Foff[k], cs[k]);
+    LGF_LAUNCH_CHECK("restrict");
+    if (k + 1 < K) {
+      const LevelPlan &Lf = P->L[k + 1];
+      k_coarsen_add<R><<<dim3(Lf.nU, ncomp), 256, 0, st>>>(Ld, Fall + Foff[k], cs[k], Lf.d_BL, Fall + Foff[k + 1],
+                                                          cs[k + 1]);
+      LGF_LAUNCH_CHECK("coarsen");
+    }
+  }
+  tm.mark(PH_RESTRICT);
+  int64_t target_cells = 0, nsrc_total = 0, ntgt_total = 0, pairs = 0;
+  // 2. coarse to fine
+  for (int k = 0; k < K; ++k) {
+    const LevelPlan &L = P->L[k];
+    const LevelDev Ld = level_dev(P, k);
+    const LevelDev Lc = k > 0 ? level_dev(P, k - 1) : Ld;
+    const int64_t ccs = k > 0 ? cs[k - 1] : 0;
+    const R *psi_prev = k > 0 ? Psi + Foff[k - 1] : nullptr;
+    R *psi_cur = Psi + Foff[k];
+    const int nSA = (int)L.SA.size(), nSB = (int)L.SB.size(), nT = L.nTall, nPhi = (int)L.Tphi.size();
+    const int nPsi = (int)L.Tpsi.size();
+    const int32_t *lists = L.d_lists;
+    if (k > 0) {
+      k_interp<R><<<dim3((unsigned)L.BL.size(), ncomp), 256, 0, st>>>(Ld, L.d_BL, c, cs[k], Lc, psi_prev, ccs);
+      LGF_LAUNCH_CHECK("interp");
+      tm.mark(PH_INTERP);
+    }
+    if (nSA) {
+      k_correct<R><<<dim3(nSA, ncomp), 256, 0, st>>>(Ld, L.d_BL, lists + L.off_SA, f, dtype, ucs, A, cs[k], c, Lc,
+                                                     psi_prev, ccs, k > 0);
+      LGF_LAUNCH_CHECK("correct");
+      tm.mark(PH_CORRECT);
+      if ((rc = PairOps<R>::forward(B, A, 2, cs[k], lists + L.off_SA, nSA, ncomp, FA, nullptr, 0, st))) return rc;
+      ++launches;
+    }
+    if (nSB) {
+      if ((rc = PairOps<R>::forward(B, Fall + Foff[k], 2, cs[k], lists + L.off_SB, nSB, ncomp, FB, L.d_cellmask,
+                                    CB_COV, st)))
+        return rc;
+      ++launches;
+    }
+    tm.mark(PH_FORWARD);
+    const double scale = L.h * L.h / (double)((2 * B) * (2 * B) * (2 * B));
+    const int64_t pcs = (int64_t)nT * W;
+    if (nSA) {
+      if ((rc = PairOps<R>::mac(B, FA, nSA, (int64_t)nSA * W, lists + L.off_SA, L.d_BL, Gh, t->mo, Phi, nT, pcs,
+                                lists + L.off_Tall, L.d_BL, ncomp, 0, st)))
+        return rc;
+    } else {
+      cudaMemsetAsync(Phi, 0, sizeof(cx<R>) * (size_t)ncomp * nT * W, st);
+    }
+    launches += (ncomp + 2) / 3;
+    pairs += (int64_t)nSA * nT;
+    tm.mark(PH_MAC);
+    if (nPsi) {
+      if ((rc = PairOps<R>::inverse(B, Phi, pcs, lists + L.off_psi, lists + L.off_Tpsi, nPsi, ncomp, psi_cur, 2,
+                                    cs[k], 0, k > 0 ? c : nullptr, cs[k], nullptr, 0, scale, st)))
+        return rc;
+      ++launches;
+    }
+    tm.mark(PH_INVERSE);
+    if (nSB && nPhi) {
+      if ((rc = PairOps<R>::mac(B, FB, nSB, (int64_t)nSB * W, lists + L.off_SB, L.d_BL, Gh, t->mo, Phi, nPhi, pcs,
+                                lists + L.off_Tall, L.d_BL, ncomp, 1, st)))
+        return rc;
+      launches += (ncomp + 2) / 3;
+      pairs += (int64_t)nSB * nPhi;
+      tm.mark(PH_MAC);
+    }
+    if (nPhi) {
+      if ((rc = PairOps<R>::inverse(B, Phi, pcs, nullptr, lists + L.off_Tall, nPhi, ncomp, phi, dtype, ucs,
+                                    L.user_off, k > 0 ? c : nullptr, cs[k], L.d_cellmask, CB_OM, scale, st)))
+        return rc;
+      ++launches;
+    }
+    tm.mark(PH_INVERSE);
+    target_cells += L.n_omega;
+    nsrc_total += nSA + nSB;
+    ntgt_total += nT;
+  }
+  // 3. residual
+  double resid = 0.0;
+  if (o.residual) {
+    cudaMemsetAsync(racc, 0, sizeof(unsigned long long) * 2 * K, st);
+    for (int k = 0; k < K; ++k) {
+      const LevelPlan &L = P->L[k];
+      if (L.Tphi.empty()) continue;
+      const LevelDev Ld = level_dev(P, k);
+      const LevelDev Lc = k > 0 ? level_dev(P, k - 1) : Ld;
+      k_residual<R><<<dim3((unsigned)L.Tphi.size(), ncomp), 256, 0, st>>>(
+          Ld, L.d_BL, L.d_lists + L.off_Tall, phi, dtype, ucs, Fall + Foff[k], cs[k], Lc,
+          k > 0 ? Psi + Foff[k - 1] : nullptr, k > 0 ? cs[k - 1] : 0, k > 0, racc + 2 * k);
+      LGF_LAUNCH_CHECK("residual");
+    }
+    std::vector<unsigned long long> h(2 * K);
+    cudaMemcpyAsync(h.data(), racc, sizeof(unsigned long long) * 2 * K, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return set_error(LGF_E_CUDA, "residual failed");
+    for (int k = 0; k < K; ++k) {
+      double r, s;
+      memcpy(&r, &h[2 * k], 8);
+      memcpy(&s, &h[2 * k + 1], 8);
+      if (s > 0) resid = std::max(resid, r / s);
+    }
+    tm.mark(PH_RESIDUAL);
+  }
+  tm.finish(rep);
+  if (rep) {
+    rep->residual_rel = resid;
+    rep->target_cells = target_cells;
+    rep->source_blocks = nsrc_total;
+    rep->target_blocks = ntgt_total;
+    rep->pairs = pairs;
+    rep->scratch_bytes = (int64_t)ws->total() + (int64_t)P->device_bytes;
+    rep->kernel_launches = launches;
+    rep->mac_mode_used = LGF_MAC_PAIR;
+  }
+  if (o.residual && o.residual_tol > 0 && resid > o.residual_tol)
+    return set_error(LGF_E_PRECISION, "FP64 residual %.3e exceeds the tolerance %.3e", resid, o.residual_tol);
+  if (o.timing) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(LGF_E_CUDA, "solve failed: %s", cudaGetErrorString(e));
+  }
+  return LGF_OK;
+}
+
+int solve_multi(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
+                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  switch (o.precision) {
+    case LGF_PREC_FP64: return solve_multi_t<double>(t, m, ncomp, f, phi, dtype, o, rep, st);
+    case LGF_PREC_FP32: return solve_multi_t<float>(t, m, ncomp, f, phi, dtype, o, rep, st);
+    default: return solve_multi_t<df>(t, m, ncomp, f, phi, dtype, o, rep, st);
+  }
+}
+
+// ------------------------------------------------------------------ heat apply
+// e^{-x} I_n(x), n <= nmax, by Miller's backward recurrence normalised with the generating-function
+// sum e^{-x} (I_0 + 2 sum I_n) = 1 (host, FP64).
+static void scaled_bessel(double x, int nmax, double *out) {
+  for (int n = 0; n <= nmax; ++n) out[n] = 0.0;
+  if (x <= 0.0) {
+    out[0] = 1.0;
+    return;
+  }
+  const int M = nmax + 60 + (int)std::sqrt(120.0 * x);
+  double tot = 0.0;
+  std::vector<double> v(M + 2, 0.0);
+  v[M] = 1e-30;
+  for (int n = M; n >= 1; --n) {
+    const double lo = (2.0 * n / x) * v[n] + v[n + 1];
+    v[n - 1] = lo;
+    if (lo > 1e200) {
+      for (int j = n - 1; j <= M; ++j) v[j] *= 1e-200;
+    }
+  }
+  tot = v[0];
+  for (int n = 1; n <= M; ++n) tot += 2.0 * v[n];
+  for (int n = 0; n <= nmax; ++n) out[n] = v[n] / tot;
+}
+
+static int heat_weights(double alpha, HeatW *w) {
+  double tmp[80];
+  scaled_bessel(2.0 * alpha, 79, tmp);
+  int r = -1;
+  for (int n = 0; n < 80; ++n) {
+    if (tmp[n] < 1e-18) break;
+    r = n;
+  }
+  if (r < 0) r = 0;
+  if (r > 64) return set_error(LGF_E_UNSUPPORTED, "heat kernel radius %d above 64 (alpha %.3g too large)", r, alpha);
+  w->r = r;
+  for (int n = 0; n <= 64; ++n) w->w[n] = n <= r ? tmp[n] : 0.0;
+  return LGF_OK;
+}
+
+template <class R>
+static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype, double alpha,
+                  const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  const int K = m->nlevels;
+  std::vector<HeatW> W(K);
+  std::vector<int> radii(K);
+  int rc;
+  for (int k = 0; k < K; ++k) {
+    if ((rc = heat_weights(alpha * std::pow(4.0, -(double)(K - 1 - k)), &W[k]))) return rc;
+    radii[k] = W[k].r;
+  }
+  Plan *P = nullptr;
+  if ((rc = get_plan(m, radii.data(), &P))) return rc;
+  const int B = P->B;
+  const int64_t B3 = (int64_t)B * B * B;
+  int64_t total_user = 0, maxBL = 0;
+  for (int k = 0; k < K; ++k) total_user += P->L[k].nU, maxBL = std::max<int64_t>(maxBL, P->L[k].BL.size());
+  const int64_t ucs = total_user * B3;
+  std::vector<int64_t> Foff(K + 1, 0), cs(K);
+  for (int k = 0; k < K; ++k) {
+    cs[k] = (int64_t)P->L[k].BL.size() * B3;
+    Foff[k + 1] = Foff[k] + ncomp * cs[k];
+  }
+  Workspace *ws = workspace_for(t, st);
+  const size_t field = sizeof(R) * (size_t)ncomp * maxBL * B3;
+  if ((rc = ws->buf[10].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[11].reserve(field)) ||
+      (rc = ws->buf[12].reserve(field)) || (rc = ws->buf[13].reserve(field)) || (rc = ws->buf[14].reserve(field)))
+    return rc;
+  R *Fall = (R *)ws->buf[10].p, *T0 = (R *)ws->buf[11].p, *T1 = (R *)ws->buf[12].p;
+  R *Uprev = (R *)ws->buf[13].p, *Ucur = (R *)ws->buf[14].p;
+  int64_t launches = 0;
+  PhaseTimer tm;
+  tm.start(o.timing != 0, st);
+  for (int k = K - 1; k >= 0; --k) {
+    const LevelPlan &L = P->L[k];
+    const LevelDev Ld = level_dev(P, k);
+    k_restrict<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, f, dtype, ucs, L.user_off, Fall + Foff[k], cs[k]);
+    LGF_LAUNCH_CHECK("restrict");
+    if (k + 1 < K) {
+      const LevelPlan &Lf = P->L[k + 1];
+      k_coarsen_add<R><<<dim3(Lf.nU, ncomp), 256, 0, st>>>(Ld, Fall + Foff[k], cs[k], Lf.d_BL, Fall + Foff[k + 1],
+                                                          cs[k + 1]);
+      LGF_LAUNCH_CHECK("coarsen");
+    }
+  }
+  tm.mark(PH_RESTRICT);
+  int64_t target_cells = 0;
+  for (int k = 0; k < K; ++k) {
+    const LevelPlan &L = P->L[k];
+    const LevelDev Ld = level_dev(P, k);
+    const LevelDev Lc = k > 0 ? level_dev(P, k - 1) : Ld;
+    const int nHB = (int)L.HB.size();
+    const int32_t *HB = L.d_lists + L.off_HB;
+    const size_t bytes = sizeof(R) * (size_t)ncomp * L.BL.size() * B3;
+    cudaMemsetAsync(T0, 0, bytes, st);
+    cudaMemsetAsync(T1, 0, bytes, st);
+    if (k + 1 < K) {
+      cudaMemsetAsync(Ucur, 0, bytes, st);
+      k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 0, f, dtype, ucs, Fall + Foff[k], L.nU, Ucur,
+                                                        cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
+      LGF_LAUNCH_CHECK("heat U");
+    }
+    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 1, f, dtype, ucs, Fall + Foff[k], L.nU, T0,
+                                                      cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
+    LGF_LAUNCH_CHECK("heat source");
+    tm.mark(PH_INTERP);
+    k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 0, T0, T1, cs[k], W[k]);
+    LGF_LAUNCH_CHECK("heat x");
+    k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 1, T1, T0, cs[k], W[k]);
+    LGF_LAUNCH_CHECK("heat y");
+    k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 2, T0, T1, cs[k], W[k]);
+    LGF_LAUNCH_CHECK("heat z");
+    k_heat_store<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, T1, cs[k], g, dtype, ucs, L.user_off);
+    LGF_LAUNCH_CHECK("heat store");
+    tm.mark(PH_HEAT);
+    target_cells += L.n_omega;
+    std::swap(Uprev, Ucur);
+  }
+  tm.finish(rep);
+  if (rep) {
+    rep->target_cells = target_cells;
+    rep->kernel_launches = launches;
+    rep->scratch_bytes = (int64_t)ws->total() + (int64_t)P->device_bytes;
+  }
+  if (o.timing) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(LGF_E_CUDA, "heat apply failed: %s", cudaGetErrorString(e));
+  }
+  return LGF_OK;
+}
+
+int solve_heat(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype, double alpha,
+               const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  if (o.precision == LGF_PREC_FP32) return heat_t<float>(t, m, ncomp, f, g, dtype, alpha, o, rep, st);
+  return heat_t<double>(t, m, ncomp, f, g, dtype, alpha, o, rep, st);
+}
+
+}  // namespace lgf

@@ -121,11 +121,14 @@ static int solve_static(const lgf_table *t, const lgf_mesh *m, int ncomp, const 
   cudaMemcpyAsync(d_tgt_c, tgt_c.data(), sizeof(int4) * ntgt, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_tgt_idx, tgt_idx.data(), sizeof(int32_t) * ntgt, cudaMemcpyHostToDevice, st);
   const int64_t cs = (int64_t)nb * B * B * B;
-  if ((rc = PairOps<R>::forward(B, f, dtype, cs, d_src_idx, nsrc, ncomp, F, st))) return rc;
-  if ((rc = PairOps<R>::mac(B, F, nsrc, d_src_c, Gh, t->mo, P, ntgt, d_tgt_c, ncomp, 0, st))) return rc;
+  if ((rc = PairOps<R>::forward(B, f, dtype, cs, d_src_idx, nsrc, ncomp, F, nullptr, 0, st))) return rc;
+  if ((rc = PairOps<R>::mac(B, F, nsrc, (int64_t)nsrc * W, nullptr, d_src_c, Gh, t->mo, P, ntgt, (int64_t)ntgt * W,
+                            nullptr, d_tgt_c, ncomp, 0, st)))
+    return rc;
   const double h = m->h0;
   const double scale = h * h / (double)((2 * B) * (2 * B) * (2 * B));
-  return PairOps<R>::inverse(B, P, ntgt, ncomp, d_tgt_idx, phi, dtype, cs, nullptr, 0, scale, st);
+  return PairOps<R>::inverse(B, P, (int64_t)ntgt * W, nullptr, d_tgt_idx, ntgt, ncomp, phi, dtype, cs, 0, nullptr, 0,
+                             nullptr, 0, scale, st);
 }
 
 int check_mesh(const lgf_mesh *m, int B_expected);

@@ -80,25 +80,30 @@ template <class R, int B>
 __global__ void __launch_bounds__(256) k_block_fwd(const void *__restrict__ f, int dtype,
                                                    int64_t comp_stride,
                                                    const int32_t *__restrict__ src_idx, int nsrc,
-                                                   cx<R> *__restrict__ out, Tw64<R> tw) {
+                                                   cx<R> *__restrict__ out,
+                                                   const uint8_t *__restrict__ cellmask, int bits,
+                                                   Tw64<R> tw) {
   using G = PairGeom<B>;
   extern __shared__ unsigned char smem_raw[];
   cx<R> *A1 = reinterpret_cast<cx<R> *>(smem_raw);
   cx<R> *A2 = A1 + G::A1;
   const int comp = blockIdx.y;
-  const int64_t base = comp * comp_stride + (int64_t)src_idx[blockIdx.x] * (B * B * B);
+  const int64_t blk = src_idx[blockIdx.x];
+  const int64_t base = comp * comp_stride + blk * (B * B * B);
+  const uint8_t *cm = cellmask ? cellmask + blk * (B * B * B) : nullptr;
   cx<R> *spec = out + ((int64_t)comp * nsrc + blockIdx.x) * G::W;
+  auto ld = [&](int64_t cell) {  // cell index inside the block
+    if (cm && !(cm[cell] & bits)) return RT<R>::zero();
+    return load_field<R>(f, base + cell, dtype);
+  };
 
   // x pass: rows y0 = 2 yp, y1 = 2 yp + 1 packed as one complex signal a + i b
   for (int t = threadIdx.x; t < B * B / 2; t += blockDim.x) {
     const int z = t / (B / 2), yp = t % (B / 2);
-    const int64_t r0 = base + ((int64_t)z * B + 2 * yp) * B;
+    const int64_t r0 = ((int64_t)z * B + 2 * yp) * B;
     cx<R> *S = A2;  // scratch: S[k * (B*B/2) + t], k < 2B
     dft_pad_fwd<R, B>(
-        tw,
-        [&](int j) {
-          return cx<R>{load_field<R>(f, r0 + j, dtype), load_field<R>(f, r0 + B + j, dtype)};
-        },
+        tw, [&](int j) { return cx<R>{ld(r0 + j), ld(r0 + B + j)}; },
         [&](int k, cx<R> v) { S[k * (B * B / 2) + t] = v; });
     cx<R> *row0 = A1 + ((z * B) + 2 * yp) * G::KX;
     cx<R> *row1 = row0 + G::KX;
@@ -128,22 +133,31 @@ __global__ void __launch_bounds__(256) k_block_fwd(const void *__restrict__ f, i
 }
 
 // ------------------------------------------------------------------ inverse: spectrum -> window
-// grid (ntgt, ncomp).  out[comp * comp_stride + tgt_idx[i] * B^3 + cell] = scale * window
-//   (+ addend[same index] when addend != nullptr; addend uses the same dtype code as out).
+// grid (n, ncomp).  Target i reads spectrum row r = rows ? rows[i] : i of component `comp`
+// (spec_in + comp * spec_cs + r * W), and with a = aux[i] writes
+//   out[comp * out_cs + (a + out_off) * B^3 + cell] = scale * window (+ addend[comp * add_cs + a * B^3 + cell])
+// for the cells whose cellmask[a * B^3 + cell] has a bit of `bits` (all cells when cellmask is null).
+// The addend is an internal buffer in the arithmetic R.
 template <class R, int B>
-__global__ void __launch_bounds__(256) k_block_inv(const cx<R> *__restrict__ spec_in, int ntgt,
-                                                   const int32_t *__restrict__ tgt_idx,
+__global__ void __launch_bounds__(256) k_block_inv(const cx<R> *__restrict__ spec_in, int64_t spec_cs,
+                                                   const int32_t *__restrict__ rows,
+                                                   const int32_t *__restrict__ aux,
                                                    void *__restrict__ out, int dtype,
-                                                   int64_t comp_stride,
-                                                   const void *__restrict__ addend, int add_dtype,
+                                                   int64_t out_cs, int64_t out_off,
+                                                   const R *__restrict__ addend, int64_t add_cs,
+                                                   const uint8_t *__restrict__ cellmask, int bits,
                                                    double scale, Tw64<R> tw) {
   using G = PairGeom<B>;
   extern __shared__ unsigned char smem_raw[];
   cx<R> *A1 = reinterpret_cast<cx<R> *>(smem_raw);
   cx<R> *A2 = A1 + G::A1;
   const int comp = blockIdx.y;
-  const cx<R> *spec = spec_in + ((int64_t)comp * ntgt + blockIdx.x) * G::W;
-  const int64_t base = comp * comp_stride + (int64_t)tgt_idx[blockIdx.x] * (B * B * B);
+  const int r = rows ? rows[blockIdx.x] : (int)blockIdx.x;
+  const cx<R> *spec = spec_in + comp * spec_cs + (int64_t)r * G::W;
+  const int64_t a = aux[blockIdx.x];
+  const int64_t base = comp * out_cs + (a + out_off) * (B * B * B);
+  const R *add = addend ? addend + comp * add_cs + a * (B * B * B) : nullptr;
+  const uint8_t *cm = cellmask ? cellmask + a * (B * B * B) : nullptr;
 
   // z pass: columns (ky, kx): 2B -> window z < B
   for (int t = threadIdx.x; t < G::N2 * G::KX; t += blockDim.x) {
@@ -175,7 +189,7 @@ __global__ void __launch_bounds__(256) k_block_inv(const cx<R> *__restrict__ spe
     const cx<R> *ra = A1 + (z * B + 2 * yp) * G::KX;
     const cx<R> *rb = ra + G::KX;
     cx<R> *S = A2;  // scratch S[j * (B*B/2) + t], j < B
-    const int64_t o0 = base + ((int64_t)z * B + 2 * yp) * B;
+    const int64_t o0 = ((int64_t)z * B + 2 * yp) * B;
     dft_window_inv<R, B>(
         tw,
         [&](int k) {
@@ -189,27 +203,31 @@ __global__ void __launch_bounds__(256) k_block_inv(const cx<R> *__restrict__ spe
         [&](int j, cx<R> v) { S[j * (B * B / 2) + t] = v; },
         [&](int j, cx<R> v) {
           cx<R> zz = S[j * (B * B / 2) + t] + v;
-          R a = zz.re * sc, b = zz.im * sc;
-          if (addend) {
-            a = a + load_field<R>(addend, o0 + j, add_dtype);
-            b = b + load_field<R>(addend, o0 + B + j, add_dtype);
+          R va = zz.re * sc, vb = zz.im * sc;
+          const int64_t ca = o0 + j, cb = o0 + B + j;
+          if (add) {
+            va = va + add[ca];
+            vb = vb + add[cb];
           }
-          store_field<R>(out, o0 + j, dtype, a);
-          store_field<R>(out, o0 + B + j, dtype, b);
+          if (!cm || (cm[ca] & bits)) store_field<R>(out, base + ca, dtype, va);
+          if (!cm || (cm[cb] & bits)) store_field<R>(out, base + cb, dtype, vb);
         });
   }
 }
 
 // ------------------------------------------------------------------ block-pair MAC
 // grid (ceil(ntgt / TC), ceil(W / blockDim.x)); one thread = one frequency w and TC targets.
-//   Phi[c][t][w] (+)= sum_{s} Ghat[idx(t - s)][w] * F[c][s][w]
-// with idx(o) = ((oz + mo.z) * (2 mo.y + 1) + (oy + mo.y)) * (2 mo.x + 1) + (ox + mo.x).
+//   Phi[c * p_cs + t * W + w] (+)= sum_s Ghat[idx(T_t - S_s)][w] * F[c * f_cs + s * W + w]
+// with block coordinates S_s = coords[src_list ? src_list[s] : s] (same for targets) and
+// idx(o) = ((oz + mo.z) * (2 mo.y + 1) + (oy + mo.y)) * (2 mo.x + 1) + (ox + mo.x).
 template <class R, int TC, int NC>
-__global__ void __launch_bounds__(128) k_mac_pair(const cx<R> *__restrict__ F, int nsrc,
-                                                  const int4 *__restrict__ src_c,
+__global__ void __launch_bounds__(128) k_mac_pair(const cx<R> *__restrict__ F, int nsrc, int64_t f_cs,
+                                                  const int32_t *__restrict__ src_list,
+                                                  const int4 *__restrict__ src_coords,
                                                   const cx<R> *__restrict__ Gh, int3 mo,
-                                                  cx<R> *__restrict__ Phi, int ntgt,
-                                                  const int4 *__restrict__ tgt_c, int W,
+                                                  cx<R> *__restrict__ Phi, int ntgt, int64_t p_cs,
+                                                  const int32_t *__restrict__ tgt_list,
+                                                  const int4 *__restrict__ tgt_coords, int W,
                                                   int accumulate) {
   const int w = blockIdx.y * blockDim.x + threadIdx.x;
   if (w >= W) return;
@@ -219,7 +237,7 @@ __global__ void __launch_bounds__(128) k_mac_pair(const cx<R> *__restrict__ F, i
 #pragma unroll
   for (int i = 0; i < TC; ++i) {
     tb[i] = (t0 + i < ntgt);
-    tc[i] = tb[i] ? tgt_c[t0 + i] : make_int4(0, 0, 0, 0);
+    tc[i] = tb[i] ? tgt_coords[tgt_list ? tgt_list[t0 + i] : t0 + i] : make_int4(0, 0, 0, 0);
   }
   const int sx = 2 * mo.x + 1, sy = 2 * mo.y + 1;
   cx<R> acc[TC][NC];
@@ -228,10 +246,10 @@ __global__ void __launch_bounds__(128) k_mac_pair(const cx<R> *__restrict__ F, i
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[i][c] = cx_zero<R>();
   for (int s = 0; s < nsrc; ++s) {
-    const int4 sc = src_c[s];
+    const int4 sc = src_coords[src_list ? src_list[s] : s];
     cx<R> fv[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) fv[c] = F[((int64_t)c * nsrc + s) * W + w];
+    for (int c = 0; c < NC; ++c) fv[c] = F[c * f_cs + (int64_t)s * W + w];
 #pragma unroll
     for (int i = 0; i < TC; ++i) {
       if (!tb[i]) continue;
@@ -247,7 +265,7 @@ __global__ void __launch_bounds__(128) k_mac_pair(const cx<R> *__restrict__ F, i
     if (!tb[i]) continue;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      cx<R> *p = Phi + ((int64_t)c * ntgt + t0 + i) * W + w;
+      cx<R> *p = Phi + c * p_cs + (int64_t)(t0 + i) * W + w;
       *p = accumulate ? (*p + acc[i][c]) : acc[i][c];
     }
   }

@@ -89,16 +89,17 @@ static int solve_single(lgf_table *t, const lgf_mesh *m, int ncomp, const void *
   PhaseTimer tm;
   tm.start(o.timing != 0, st);
   const int64_t cs = (int64_t)m->nblocks[0] * B3;
-  if ((rc = PairOps<R>::forward(B, f, dtype, cs, d_src_idx, nsrc, ncomp, ws->buf[0].p, st))) return rc;
+  if ((rc = PairOps<R>::forward(B, f, dtype, cs, d_src_idx, nsrc, ncomp, ws->buf[0].p, nullptr, 0, st)))
+    return rc;
   tm.mark(PH_FORWARD);
-  if ((rc = PairOps<R>::mac(B, ws->buf[0].p, nsrc, d_src_c, Gh, t->mo, ws->buf[1].p, ntgt, d_tgt_c, ncomp,
-                            0, st)))
+  if ((rc = PairOps<R>::mac(B, ws->buf[0].p, nsrc, (int64_t)nsrc * W, nullptr, d_src_c, Gh, t->mo, ws->buf[1].p,
+                            ntgt, (int64_t)ntgt * W, nullptr, d_tgt_c, ncomp, 0, st)))
     return rc;
   tm.mark(PH_MAC);
   const double h = m->h0;
   const double scale = h * h / (double)((2 * B) * (2 * B) * (2 * B));
-  if ((rc = PairOps<R>::inverse(B, ws->buf[1].p, ntgt, ncomp, d_tgt_idx, phi, dtype, cs, nullptr, 0, scale,
-                                st)))
+  if ((rc = PairOps<R>::inverse(B, ws->buf[1].p, (int64_t)ntgt * W, nullptr, d_tgt_idx, ntgt, ncomp, phi, dtype,
+                                cs, 0, nullptr, 0, nullptr, 0, scale, st)))
     return rc;
   tm.mark(PH_INVERSE);
   tm.finish(rep);
@@ -127,16 +128,6 @@ int solve_poisson(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
     case LGF_PREC_FP32: return solve_single<float>(t, m, ncomp, f, phi, dtype, o, rep, st);
     default: return solve_single<df>(t, m, ncomp, f, phi, dtype, o, rep, st);
   }
-}
-
-int solve_multi(lgf_table *, const lgf_mesh *, int, const void *, void *, int, const lgf_solve_opts &,
-                lgf_report *, cudaStream_t) {
-  return set_error(LGF_E_UNSUPPORTED, "multi-level solve not built yet");
-}
-
-int solve_heat(lgf_table *, const lgf_mesh *, int, const void *, void *, int, double, const lgf_solve_opts &,
-               lgf_report *, cudaStream_t) {
-  return set_error(LGF_E_UNSUPPORTED, "heat apply not built yet");
 }
 
 }  // namespace lgf
