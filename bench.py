@@ -64,7 +64,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -96,6 +96,62 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+MODE_NAMES = {1: "pair", 2: "box"}
+PHASE_NAMES = ("restrict", "correction", "forward", "mac", "inverse", "interp", "residual", "heat")
+
+
+def _phases(ph):
+    return {n: float(v) for n, v in zip(PHASE_NAMES, ph) if v}
+
+
+def df_box_instructions(B, nb, nfields):
+    """FP32 instructions the double-float block-index FFT mode needs per solve (algorithmic count).
+
+    Block-index DFTs: every complex multiply-add is 72 FP32 instructions (4 TwoProd-based products
+    of 7 and 4 renormalised sums of 11 -- see common.cuh); per field the forward passes do
+    2 nb_a^2 products per line and cell, the inverse P_a nb_a.  Local FFTs: radix-2 B-point FFT =
+    (B/2) log2 B butterflies with B log2 B - ... twiddled products; per B^3 block six axis passes of
+    B^2 lines, plus the four-step twiddles (2 complex products per cell each way) and the real
+    kernel product (2 double-float products per cell).
+    """
+    import math
+    nx, ny, nz = nb
+    px, py, pz = 2 * nx, 2 * ny, 2 * nz
+    B3 = B ** 3
+    fwd = B3 * (ny * nz * 2 * nx * nx + px * nz * 2 * ny * ny + px * py * 2 * nz * nz)
+    inv = B3 * (px * py * pz * nz + px * nz * py * ny + ny * nz * px * nx)
+    dft = (fwd + inv) * 72
+    lg = int(math.log2(B))
+    twiddled = sum((B // ln) * (ln // 2 - 1) for ln in [2 ** s for s in range(1, lg + 1)])
+    fft1d = twiddled * 50 + (B // 2) * lg * 2 * 22
+    local = px * py * pz * (6 * B * B * fft1d + 4 * B3 * 50 + B3 * 2 * 7)
+    return nfields * dft, nfields * local
+
+
+def roofline_entry(case, B, ncomp, rep, ph):
+    """Roofline of the dominant kernel class of the DF32 solve (FP32-pipe bound)."""
+    W = (2 * B) ** 2 * (B + 1)
+    if rep.mac_mode_used == 1:  # pair
+        cmacs = rep.pairs * W * ncomp
+        inst = cmacs * DF_OPS_PER_CMAC
+        ms = ph[3]
+        kern, launches = "k_mac_pair<df,4,3> (block-pair multiply-accumulate)", 1
+    else:
+        nz, ny, nx = (n // B for n in case["shape"])
+        nfields = (ncomp + 1) // 2
+        dft, local = df_box_instructions(B, (nx, ny, nz), nfields)
+        if ph[3] >= ph[2] + ph[4]:
+            inst, ms, kern, launches = local, ph[3], "k_box_mid<df,16> (twiddle + local FFT + kernel + inverse)", nfields
+        else:
+            inst, ms, kern, launches = dft, ph[2] + ph[4], "k_bdft_fwd/inv<df,16> (block-index DFTs)", 6 * nfields
+    ach = inst / (ms * 1e-3)
+    return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": FP32_INST_PEAK / 1e12,
+            "unit": "T FP32-inst/s", "frac": ach / FP32_INST_PEAK, "traffic": None,
+            "launches_per_step": launches, "kernel_ms_per_step": float(ms),
+            "note": "algorithmic FP32 instructions of the double-float arithmetic / CUDA-event time of the"
+                    " kernel class; peak = 152 SMs x 128 FP32 lanes x 2070 MHz (derived, not measured)"}
 
 
 def build_case():
@@ -162,9 +218,12 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
 
-    def solve(prec, rep=None, timing=0, fin=f, fout=phi):
+    mode = {"auto": L.LGF_MAC_AUTO, "pair": L.LGF_MAC_PAIR, "box": L.LGF_MAC_BOX}[args.mode]
+
+    def solve(prec, rep=None, timing=0, fin=f, fout=phi, m=None):
         L.lgf_poisson_solve(table, mesh, ncomp, fin.data_ptr(), fout.data_ptr(), L.LGF_F64,
-                            L.make_opts(precision=prec, mac_mode=L.LGF_MAC_PAIR, timing=timing), rep, stream)
+                            L.make_opts(precision=prec, mac_mode=mode if m is None else m, timing=timing), rep,
+                            stream)
 
     # accuracy outside the timed region: against the oracle (rank 0 computes, all ranks check)
     ref = cpu_oracle_step(case)
@@ -176,29 +235,31 @@ def run_gpu(args):
         got = S.blocks_to_box(phi.cpu().numpy(), case["blocks"], B, case["shape"])
         errs[name] = float(max(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max() for c in range(2)))
 
-    def timed(prec):
+    def timed(prec, m=None):
         for _ in range(args.warmup):
-            solve(prec)
+            solve(prec, m=m)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        step_ms, mac_ms = [], []
+        step_ms, phase_ms = [], []
         rep = L.lgf_report()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1.0)  # L2 flush between timed steps (256 MiB write), outside the events
-            solve(prec, rep, timing=1)
+            solve(prec, rep, timing=1, m=m)
             step_ms.append(rep.ms_total)
-            mac_ms.append(rep.ms_phase[3])
+            phase_ms.append([rep.ms_phase[i] for i in range(8)])
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         wall = time.perf_counter() - t0
-        return float(np.mean(step_ms)), float(np.mean(mac_ms)), wall, rep
+        return float(np.mean(step_ms)), np.mean(np.array(phase_ms), axis=0), wall, rep
 
     with ClockSampler(local) as clk:
-        ms_df, mac_df, wall_df, rep_df = timed(L.LGF_PREC_DF32)
-        ms_64, mac_64, wall_64, rep_64 = timed(L.LGF_PREC_FP64)
+        ms_df, ph_df, wall_df, rep_df = timed(L.LGF_PREC_DF32)
+        ms_64, ph_64, wall_64, rep_64 = timed(L.LGF_PREC_FP64)
+        ms_32, ph_32, wall_32, rep_32 = timed(L.LGF_PREC_FP32)
+        ms_dfp, ph_dfp, _, rep_dfp = timed(L.LGF_PREC_DF32, m=L.LGF_MAC_PAIR)
     clocks = clk.summary()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -231,15 +292,7 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    W = (2 * B) ** 2 * (B + 1)
-    pairs = rep_df.pairs
-    cmacs = pairs * W * ncomp
-    ach_df = cmacs * DF_OPS_PER_CMAC / (mac_df * 1e-3)
-    roof = {"kernel": "k_mac_pair<df> (block-pair multiply-accumulate)", "bound": "alu",
-            "achieved": ach_df / 1e12, "peak": FP32_INST_PEAK / 1e12, "unit": "T FP32-inst/s",
-            "frac": ach_df / FP32_INST_PEAK, "traffic": None,
-            "note": f"{DF_OPS_PER_CMAC} FP32 instructions per double-float complex MAC x {cmacs:.3e} MACs;"
-                    " peak = 152 SMs x 128 lanes x 2070 MHz (derived)"}
+    roof = roofline_entry(case, B, ncomp, rep_df, ph_df)
     cores = os.cpu_count()
     t0 = time.perf_counter()
     cpu_oracle_step(case)
@@ -251,13 +304,17 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": cells, "ncomp": ncomp, "blocks": int(len(case["blocks"])),
-                   "mac_mode": "pair", "parallelism": f"replicas{world}",
+                   "mac_mode": args.mode, "parallelism": f"replicas{world}",
                    "l2": "flushed by a 256 MiB write between timed steps (outside the step events)"},
         "rel_err": errs,
         "fp64": {"value": cells * world / (ms_64 * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": ms_64,
-                 "mac_ms": mac_64,
-                 "mac_frac_fp64_peak": pairs * W * ncomp * 8 / (mac_64 * 1e-3) / FP64_FLOP_PEAK},
-        "phases_ms_df32": {k: v for k, v in L.lgf_report.as_dict(rep_df)["ms_phase"].items() if v},
+                 "mode": MODE_NAMES[rep_64.mac_mode_used], "phases_ms": _phases(ph_64)},
+        "fp32": {"value": cells * world / (ms_32 * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": ms_32,
+                 "rel_err": errs["fp32"], "note": "plain FP32: error above the 1e-10 target, reported only"},
+        "df32_pair_mode": {"value": cells * world / (ms_dfp * 1e-3) / 1e6, "unit": "Mcells/s",
+                           "ms_per_step": ms_dfp, "phases_ms": _phases(ph_dfp)},
+        "mode": MODE_NAMES[rep_df.mac_mode_used],
+        "phases_ms_df32": _phases(ph_df),
         "table_build_s": t_tab,
         "roofline": roof,
         "cpu_baseline": {"value": cells / cpu_dt / 1e6, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
@@ -267,7 +324,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)},
         "gpu_launches": int(rep_df.kernel_launches) * args.steps,
         "clocks": clocks,
-        "wall_s_timed": {"df32": wall_df, "fp64": wall_64},
+        "wall_s_timed": {"df32": wall_df, "fp64": wall_64, "fp32": wall_32},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -277,9 +334,10 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "pair", "box"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -135,6 +135,7 @@ int lgf_table_destroy(lgf_table *t) {
     for (auto &b : kv.second->buf) b.release();
     delete kv.second;
   }
+  for (auto &kv : t->box) delete kv.second;
   delete t;
   return LGF_OK;
 }

@@ -1,0 +1,331 @@
+// box.cuh -- block-index FFT mode: the per-frequency sum over block pairs diagonalised by a
+// zero-padded DFT over the level's block grid (exact reformulation of the lattice convolution,
+// Sec. 2.2 Eq. (eq:lgf_convolution)).
+//
+// A level box of nb = (nbx, nby, nbz) blocks of B^3 cells is embedded in a periodic lattice of
+// P = 2 nb blocks per axis (Pc = P B cells), large enough that the circular convolution with the
+// circularly laid out LGF equals the linear one on the box.  Writing a cell index n = B J + m (block J,
+// local cell m) and a frequency K = K1 + P K2 (K1 in [0, P), K2 in [0, B)) per axis, the Pc-point DFT
+// factors as ("four-step"):
+//     Y[K1][m]  = sum_J x[J][m] W_P^{J.K1}                  block-index DFT   (k_bdft_fwd, per axis)
+//     Y'        = Y W_Pc^{m.K1}                              twiddle          (k_box_mid)
+//     X[K1][K2] = sum_m Y'[K1][m] W_B^{m.K2}                 local B^3 FFT     (k_box_mid)
+// The convolution multiplies X by the (real, since G is even) spectrum Ghat[K1][K2] and runs the three
+// steps backwards; the inverse block-index DFT is evaluated only on the box's blocks.  Inputs are
+// complex: two real fields ride as real and imaginary part (G is real).
+//
+// The block-index DFTs have P = 2 nb points of which only nb inputs (forward) or outputs (inverse)
+// are used; they are evaluated directly (W_P^{(j k) mod P} from a table), the forward in two halves of
+// nb outputs (even and odd k) to bound the accumulators.
+#pragma once
+#include "common.cuh"
+
+#define BOX_NB_MAX 16
+
+template <class R>
+struct BoxTw {  // W_P^n = e^{-2 pi i n / P}, n < P = 2 nb of the pass's axis
+  cx<R> w[2 * BOX_NB_MAX];
+};
+
+// Layout of a box array: [bz][by][bx][B^3] with full extents (Px, Py, Pz) blocks.
+struct BoxGeom {
+  int nb[3];    // box blocks per axis
+  int P[3];     // 2 nb
+  int64_t bs[3];  // block strides (in blocks) of the full P-array: 1, Px, Px*Py
+};
+
+// Source of the first forward pass: box block -> buffer block (gather, -1 = absent), a field
+// (dtype per load_field, the component already applied to the pointer) and an optional cell mask.
+// Each spec adds into the real (part 0) or the imaginary (part 1) part of the complex input.
+struct InSpec {
+  const int32_t *gather;
+  const void *src;
+  const uint8_t *mask;
+  int dtype, bits, part;
+};
+// Destination of the last inverse pass for the real (re) or imaginary (im) part: box block ->
+// output block (scatter, -1 = skip), output field (component applied) with element offset, the
+// internal-R addend and mask indexed by aux (or by the output block when aux is null).
+template <class R>
+struct OutSpec {
+  const int32_t *scatter;
+  const int32_t *aux;
+  void *dst;
+  const R *add;
+  const uint8_t *mask;
+  int64_t off;
+  int dtype, bits;
+};
+
+// ------------------------------------------------------------------ block-index DFT, forward
+// Pass along axis `ax`: for every line (the two other block coordinates within `ext`) and every
+// local cell m, out[.. k ..][m] = sum_{j < nb} W_P^{j k} in[.. j ..][m], k < P.  The first pass
+// (nspec > 0) gathers its input from the specs instead of `in`.
+template <class R, int B>
+__global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
+                                                  BoxGeom g, int ax, int3 ext, BoxTw<R> tw, int nspec,
+                                                  InSpec s0, InSpec s1, InSpec s2) {
+  constexpr int B3 = B * B * B;
+  const int nb = g.nb[ax];
+  const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+  const int e1 = ax == 0 ? ext.y : ext.x;
+  const int64_t line = blockIdx.y;
+  const int l1 = (int)(line % e1), l2 = (int)(line / e1);
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= B3) return;
+  // addresses along the pass axis: box array element (base + j * bstride) * B3 + m, gather index gbase + j * gstride
+  const int64_t bsa = g.bs[ax];
+  const int64_t base = (int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2];
+  const int64_t gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1]);
+  const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
+  const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
+  const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
+  auto add_spec = [&](const InSpec &s, int64_t bidx, R &re, R &im) {
+    const int idx = s.gather[bidx];
+    if (idx < 0) return;
+    const int64_t e = (int64_t)idx * B3 + m;
+    if (s.mask && !(s.mask[e] & s.bits)) return;
+    const R v = load_field<R>(s.src, e, s.dtype);
+    if (s.part) im = im + v;
+    else re = re + v;
+  };
+  auto elem_in = [&](int j) -> cx<R> {
+    if (nspec) {
+      const int64_t bidx = gbase + j * gsa;
+      R re = RT<R>::zero(), im = RT<R>::zero();
+      add_spec(s0, bidx, re, im);
+      if (nspec > 1) add_spec(s1, bidx, re, im);
+      if (nspec > 2) add_spec(s2, bidx, re, im);
+      return cx<R>{re, im};
+    }
+    return in[(base + j * bsa) * B3 + m];
+  };
+  const int P = 2 * nb;
+  for (int half = 0; half < 2; ++half) {
+    cx<R> acc[BOX_NB_MAX];
+#pragma unroll
+    for (int k = 0; k < BOX_NB_MAX; ++k) acc[k] = cx_zero<R>();
+    for (int j = 0; j < nb; ++j) {
+      const cx<R> x = elem_in(j);
+      int n = half ? j : 0;  // (j * (2k + half)) mod P for k = 0, 1, ...
+      const int step = (2 * j) % P;
+#pragma unroll
+      for (int k = 0; k < BOX_NB_MAX; ++k) {
+        if (k < nb) acc[k] = n ? cmac(acc[k], x, tw.w[n]) : cnorm(cadd(acc[k], x));
+        n += step;
+        if (n >= P) n -= P;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < BOX_NB_MAX; ++k)
+      if (k < nb) out[(base + (int64_t)(2 * k + half) * bsa) * B3 + m] = acc[k];
+  }
+}
+
+// ------------------------------------------------------------------ block-index DFT, inverse
+// out[.. j ..][m] = sum_{k < P} W_P^{-j k} in[.. k ..][m] for j < nb (unnormalised).  The last pass
+// (final != 0) writes scale * re and scale * im through the two output specs instead of `out`.
+template <class R>
+LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
+  if (!o.scatter) return;
+  const int ob = o.scatter[bidx];
+  if (ob < 0) return;
+  const int64_t a = (int64_t)(o.aux ? o.aux[bidx] : ob) * B3 + m;
+  if (o.add) v = v + o.add[a];
+  if (o.mask && !(o.mask[a] & o.bits)) return;
+  store_field<R>(o.dst, o.off + (int64_t)ob * B3 + m, o.dtype, v);
+}
+
+template <class R, int B>
+__global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
+                                                  BoxGeom g, int ax, int3 ext, BoxTw<R> tw, int final,
+                                                  OutSpec<R> ore, OutSpec<R> oim, double scale) {
+  constexpr int B3 = B * B * B;
+  const int nb = g.nb[ax];
+  const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+  const int e1 = ax == 0 ? ext.y : ext.x;
+  const int64_t line = blockIdx.y;
+  const int l1 = (int)(line % e1), l2 = (int)(line / e1);
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= B3) return;
+  const int64_t bsa = g.bs[ax];
+  const int64_t base = (int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2];
+  const int P = 2 * nb;
+  cx<R> acc[BOX_NB_MAX];
+#pragma unroll
+  for (int j = 0; j < BOX_NB_MAX; ++j) acc[j] = cx_zero<R>();
+  for (int k = 0; k < P; ++k) {
+    const cx<R> x = in[(base + k * bsa) * B3 + m];
+    int n = 0;  // (j * k) mod P for j = 0, 1, ...
+#pragma unroll
+    for (int j = 0; j < BOX_NB_MAX; ++j) {
+      if (j < nb) acc[j] = n ? cmac(acc[j], x, conj(tw.w[n])) : cnorm(cadd(acc[j], x));
+      n += k;
+      if (n >= P) n -= P;
+    }
+  }
+  if (!final) {
+#pragma unroll
+    for (int j = 0; j < BOX_NB_MAX; ++j)
+      if (j < nb) out[(base + (int64_t)j * bsa) * B3 + m] = acc[j];
+    return;
+  }
+  const R sc = RT<R>::from(scale);
+  const int64_t gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1]);
+  const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
+  const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
+  const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
+#pragma unroll
+  for (int j = 0; j < BOX_NB_MAX; ++j) {
+    if (j >= nb) continue;
+    const int bidx = (int)(gbase + j * gsa);
+    box_store<R>(ore, bidx, m, B3, acc[j].re * sc);
+    box_store<R>(oim, bidx, m, B3, acc[j].im * sc);
+  }
+}
+
+// ------------------------------------------------------------------ dense block-index DFT (kernel spectra, FP64)
+// out[.. k ..][m] = sum_{j < P} W_P^{j k} in[.. j ..][m] over all P blocks; the first pass reads the
+// circularly laid out unit-lattice LGF: cell n (per axis, 0 <= n < Pc) holds G(d), d = n for
+// n <= Pc/2 and n - Pc above.
+template <int B>
+__global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict__ in, cx<double> *__restrict__ out,
+                                                    BoxGeom g, int ax, const cx<double> *__restrict__ wP,
+                                                    const double *__restrict__ Gd, int K) {
+  constexpr int B3 = B * B * B;
+  const int P = g.P[ax];
+  const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+  const int e1 = g.P[a1];
+  const int64_t line = blockIdx.y;
+  const int l1 = (int)(line % e1), l2 = (int)(line / e1);
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= B3) return;
+  int coord[3];
+  coord[a1] = l1;
+  coord[a2] = l2;
+  const int mloc[3] = {m % B, (m / B) % B, m / (B * B)};
+  auto value = [&](int j) -> cx<double> {
+    coord[ax] = j;
+    if (Gd) {
+      int d[3];
+      for (int a = 0; a < 3; ++a) {
+        const int Pc = g.P[a] * B, n = coord[a] * B + mloc[a];
+        d[a] = n <= Pc / 2 ? n : Pc - n;
+      }
+      return cx<double>{Gd[((int64_t)d[2] * K + d[1]) * K + d[0]], 0.0};
+    }
+    return in[((int64_t)coord[0] * g.bs[0] + coord[1] * g.bs[1] + coord[2] * g.bs[2]) * B3 + m];
+  };
+  for (int k = 0; k < P; ++k) {
+    cx<double> acc{0.0, 0.0};
+    for (int j = 0; j < P; ++j) acc = acc + value(j) * wP[(j * k) % P];
+    coord[ax] = k;
+    out[((int64_t)coord[0] * g.bs[0] + coord[1] * g.bs[1] + coord[2] * g.bs[2]) * B3 + m] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ fused twiddle + local FFT + kernel
+// One CTA per K1 block: Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat[K1][.]; back.
+// Shared memory: B^3 complex with x rows padded to B+1.
+template <int B>
+struct MidGeom {
+  static constexpr int RS = B + 1;          // padded row
+  static constexpr int N = B * B * RS;      // padded elements
+};
+
+template <class R, int B, bool MULTIPLY>
+__global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, const R *__restrict__ Gh, BoxGeom g,
+                                                 const cx<R> *__restrict__ twx, const cx<R> *__restrict__ twy,
+                                                 const cx<R> *__restrict__ twz, Tw64<R> tw, R *__restrict__ kout) {
+  constexpr int B3 = B * B * B, RS = B + 1;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
+  __shared__ cx<R> T[3][B];
+  const int64_t kb = blockIdx.x;  // K1 block, linear in the full P array
+  const int k1x = (int)(kb % g.P[0]), k1y = (int)((kb / g.P[0]) % g.P[1]), k1z = (int)(kb / ((int64_t)g.P[0] * g.P[1]));
+  const int Pcx = g.P[0] * B, Pcy = g.P[1] * B, Pcz = g.P[2] * B;
+  if (threadIdx.x < 3 * B) {
+    const int a = threadIdx.x / B, mm = threadIdx.x % B;
+    const int k1 = a == 0 ? k1x : (a == 1 ? k1y : k1z);
+    const int Pc = a == 0 ? Pcx : (a == 1 ? Pcy : Pcz);
+    const cx<R> *tab = a == 0 ? twx : (a == 1 ? twy : twz);
+    T[a][mm] = tab[(int)(((int64_t)mm * k1) % Pc)];
+  }
+  cx<R> *Yb = Y + kb * B3;
+  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
+    const int x = i % B, y = (i / B) % B, z = i / (B * B);
+    S[(z * B + y) * RS + x] = Yb[i];
+  }
+  __syncthreads();
+  // forward: x lines with the full twiddle, then y, then z
+  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
+    const int y = line % B, z = line / B;
+    const cx<R> tyz = cmul(T[1][y], T[2][z]);
+    cx<R> v[B];
+#pragma unroll
+    for (int x = 0; x < B; ++x) v[x] = cmul(S[(z * B + y) * RS + x], cmul(T[0][x], tyz));
+    fft_reg<R, B, false>(v, tw);
+#pragma unroll
+    for (int x = 0; x < B; ++x) S[(z * B + y) * RS + x] = v[x];
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
+    const int x = line % B, z = line / B;
+    cx<R> v[B];
+#pragma unroll
+    for (int y = 0; y < B; ++y) v[y] = S[(z * B + y) * RS + x];
+    fft_reg<R, B, false>(v, tw);
+#pragma unroll
+    for (int y = 0; y < B; ++y) S[(z * B + y) * RS + x] = v[y];
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
+    const int x = line % B, y = line / B;
+    cx<R> v[B];
+#pragma unroll
+    for (int z = 0; z < B; ++z) v[z] = S[(z * B + y) * RS + x];
+    fft_reg<R, B, false>(v, tw);
+    if (MULTIPLY) {
+      // X[K1][K2] *= Ghat, K2 = (x, y, z) local frequency, then inverse z
+#pragma unroll
+      for (int z = 0; z < B; ++z) {
+        const R gk = Gh[kb * B3 + (z * B + y) * B + x];
+        v[z] = cx<R>{v[z].re * gk, v[z].im * gk};
+      }
+      fft_reg<R, B, true>(v, tw);
+#pragma unroll
+      for (int z = 0; z < B; ++z) S[(z * B + y) * RS + x] = v[z];
+    } else {
+      // kernel-spectrum generation: store the real part of X (G even => X real)
+#pragma unroll
+      for (int z = 0; z < B; ++z) kout[kb * B3 + (z * B + y) * B + x] = v[z].re;
+    }
+  }
+  if (!MULTIPLY) return;
+  __syncthreads();
+  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
+    const int x = line % B, z = line / B;
+    cx<R> v[B];
+#pragma unroll
+    for (int y = 0; y < B; ++y) v[y] = S[(z * B + y) * RS + x];
+    fft_reg<R, B, true>(v, tw);
+#pragma unroll
+    for (int y = 0; y < B; ++y) S[(z * B + y) * RS + x] = v[y];
+  }
+  __syncthreads();
+  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
+    const int y = line % B, z = line / B;
+    const cx<R> tyz = conj(cmul(T[1][y], T[2][z]));
+    cx<R> v[B];
+#pragma unroll
+    for (int x = 0; x < B; ++x) v[x] = S[(z * B + y) * RS + x];
+    fft_reg<R, B, true>(v, tw);
+#pragma unroll
+    for (int x = 0; x < B; ++x) S[(z * B + y) * RS + x] = cmul(v[x], cmul(conj(T[0][x]), tyz));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
+    const int x = i % B, y = (i / B) % B, z = i / (B * B);
+    Yb[i] = S[(z * B + y) * RS + x];
+  }
+}

@@ -1,0 +1,112 @@
+// box_ops.cuh -- host launch sequence of one block-index-FFT convolution (instantiated per arithmetic).
+#pragma once
+#include <type_traits>
+
+#include "box.cuh"
+#include "internal.h"
+
+namespace lgf {
+
+template <class R>
+inline const R *spec_of(const BoxSpec *S);
+template <>
+inline const double *spec_of<double>(const BoxSpec *S) { return S->g64; }
+template <>
+inline const float *spec_of<float>(const BoxSpec *S) { return S->g32; }
+template <>
+inline const df *spec_of<df>(const BoxSpec *S) { return S->gdf; }
+
+template <class R>
+inline const cx<R> *tw_of(const BoxSpec *S, int a);
+template <>
+inline const cx<double> *tw_of<double>(const BoxSpec *S, int a) { return S->tw64[a]; }
+template <>
+inline const cx<float> *tw_of<float>(const BoxSpec *S, int a) { return S->tw32[a]; }
+template <>
+inline const cx<df> *tw_of<df>(const BoxSpec *S, int a) { return S->twdf[a]; }
+
+inline void btw_fill(BoxTw<double> &t, const BoxSpec *S, int a) {
+  for (int i = 0; i < 2 * BOX_NB_MAX; ++i) t.w[i] = S->bw64[a][i];
+}
+inline void btw_fill(BoxTw<float> &t, const BoxSpec *S, int a) {
+  for (int i = 0; i < 2 * BOX_NB_MAX; ++i) t.w[i] = S->bw32[a][i];
+}
+inline void btw_fill(BoxTw<df> &t, const BoxSpec *S, int a) {
+  for (int i = 0; i < 2 * BOX_NB_MAX; ++i) t.w[i] = S->bwdf[a][i];
+}
+template <class R>
+inline BoxTw<R> btw_of(const BoxSpec *S, int a) {
+  BoxTw<R> t;
+  btw_fill(t, S, a);
+  return t;
+}
+
+template <class R>
+struct BoxOps {
+  // Convolution of one complex field on the box: forward (gathering from the specs), kernel,
+  // inverse (scattering through the output specs).  Y0/Y1: P^3 B^3 complex R each.
+  // `mark(phase)` is called after the forward, kernel and inverse stages (phase timing; may be null).
+  static int convolve(int B, const BoxSpec *S, int nspec, const InSpec *in, const OutSpec<R> &ore,
+                      const OutSpec<R> &oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
+                      void (*mark)(void *, int) = nullptr, void *mark_ctx = nullptr);
+};
+
+template <class R, int B>
+static int box_convolve_b(const BoxSpec *S, int nspec, const InSpec *in, const OutSpec<R> &ore,
+                          const OutSpec<R> &oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
+                          void (*mark)(void *, int), void *mark_ctx) {
+  constexpr int B3 = B * B * B;
+  BoxGeom g;
+  for (int a = 0; a < 3; ++a) {
+    g.nb[a] = S->nb[a];
+    g.P[a] = 2 * S->nb[a];
+  }
+  g.bs[0] = 1;
+  g.bs[1] = g.P[0];
+  g.bs[2] = (int64_t)g.P[0] * g.P[1];
+  const unsigned gx = (B3 + 255) / 256;
+  InSpec sp[3] = {};
+  for (int i = 0; i < nspec && i < 3; ++i) sp[i] = in[i];
+  const int *nb = g.nb, *P = g.P;
+  // forward x (gather), y, z
+  k_bdft_fwd<R, B><<<dim3(gx, nb[1] * nb[2]), 256, 0, st>>>(nullptr, Y0, g, 0, make_int3(0, nb[1], nb[2]),
+                                                            btw_of<R>(S, 0), nspec, sp[0], sp[1], sp[2]);
+  k_bdft_fwd<R, B><<<dim3(gx, P[0] * nb[2]), 256, 0, st>>>(Y0, Y1, g, 1, make_int3(P[0], 0, nb[2]),
+                                                           btw_of<R>(S, 1), 0, sp[0], sp[1], sp[2]);
+  k_bdft_fwd<R, B><<<dim3(gx, P[0] * P[1]), 256, 0, st>>>(Y1, Y0, g, 2, make_int3(P[0], P[1], 0),
+                                                          btw_of<R>(S, 2), 0, sp[0], sp[1], sp[2]);
+  if (mark) mark(mark_ctx, 2);
+  // fused twiddle / local FFT / kernel / inverse
+  const size_t sm = sizeof(cx<R>) * (size_t)B * B * (B + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_box_mid<R, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  const int64_t nblk = (int64_t)P[0] * P[1] * P[2];
+  k_box_mid<R, B, true><<<(unsigned)nblk, 256, sm, st>>>(Y0, spec_of<R>(S), g, tw_of<R>(S, 0), tw_of<R>(S, 1),
+                                                         tw_of<R>(S, 2), make_tw64<R>(), nullptr);
+  if (mark) mark(mark_ctx, 3);
+  // inverse z, y, x (scatter)
+  OutSpec<R> none{};
+  k_bdft_inv<R, B><<<dim3(gx, P[0] * P[1]), 256, 0, st>>>(Y0, Y1, g, 2, make_int3(P[0], P[1], 0), btw_of<R>(S, 2),
+                                                          0, none, none, 1.0);
+  k_bdft_inv<R, B><<<dim3(gx, P[0] * nb[2]), 256, 0, st>>>(Y1, Y0, g, 1, make_int3(P[0], 0, nb[2]),
+                                                           btw_of<R>(S, 1), 0, none, none, 1.0);
+  k_bdft_inv<R, B><<<dim3(gx, nb[1] * nb[2]), 256, 0, st>>>(Y0, Y1, g, 0, make_int3(0, nb[1], nb[2]),
+                                                            btw_of<R>(S, 0), 1, ore, oim, scale);
+  if (mark) mark(mark_ctx, 4);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "box convolution launch: %s", cudaGetErrorString(e));
+}
+
+template <class R>
+int BoxOps<R>::convolve(int B, const BoxSpec *S, int nspec, const InSpec *in, const OutSpec<R> &ore,
+                        const OutSpec<R> &oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
+                        void (*mark)(void *, int), void *mark_ctx) {
+  if (B == 8) return box_convolve_b<R, 8>(S, nspec, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
+  if (B == 16) return box_convolve_b<R, 16>(S, nspec, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
+  return set_error(LGF_E_UNSUPPORTED, "block size %d", B);
+}
+
+}  // namespace lgf

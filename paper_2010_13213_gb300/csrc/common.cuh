@@ -107,6 +107,88 @@ LGF_D cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
 template <class R>
 LGF_D cx<R> cx_zero() { return {RT<R>::zero(), RT<R>::zero()}; }
 
+// ------------------------------------------------------------------ fused complex kernels
+// cadd / csub / cmul / cmac: the complex sum, difference, product and multiply-add.  For double and
+// float they are plain (contracted) arithmetic; for double-float they are fused error-free forms:
+//   cmul: each real part is a two-term dot product: both hi*hi products by TwoProd, the four cross
+//         products folded into one correction, one TwoSum, one renormalisation (19 instructions);
+//   cmac: the same with the accumulator: two TwoSums, one renormalisation (27 instructions per part);
+//   cadd/csub: TwoSum of the hi parts plus the lo parts, left unnormalised ("lazy"): callers
+//         renormalise with cnorm before a value is stored (8 instructions per part instead of 11).
+template <class R>
+LGF_D cx<R> cadd(cx<R> a, cx<R> b) { return a + b; }
+template <class R>
+LGF_D cx<R> csub(cx<R> a, cx<R> b) { return a - b; }
+template <class R>
+LGF_D cx<R> cmul(cx<R> a, cx<R> b) { return a * b; }
+template <class R>
+LGF_D cx<R> cnorm(cx<R> a) { return a; }
+LGF_D cx<double> cmac(cx<double> acc, cx<double> a, cx<double> b) {
+  return {fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
+}
+LGF_D cx<float> cmac(cx<float> acc, cx<float> a, cx<float> b) {
+  return {fmaf(a.re, b.re, fmaf(-a.im, b.im, acc.re)), fmaf(a.re, b.im, fmaf(a.im, b.re, acc.im))};
+}
+
+LGF_D df df_add_lazy(df a, df b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return {s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+LGF_D df df_sub_lazy(df a, df b) { return df_add_lazy(a, df{-b.hi, -b.lo}); }
+LGF_D df df_renorm(df a) {
+  float hi = __fadd_rn(a.hi, a.lo);
+  return {hi, __fsub_rn(a.lo, __fsub_rn(hi, a.hi))};
+}
+// a*b + sgn * c*d with error-free products (sgn = +1 or -1)
+LGF_D df df_dot2(df a, df b, df c, df d, float sgn) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  const float p2 = __fmul_rn(sgn * c.hi, d.hi);
+  const float e2 = __fmaf_rn(sgn * c.hi, d.hi, -p2);
+  float x = __fmaf_rn(a.lo, b.hi, e1);
+  x = __fmaf_rn(a.hi, b.lo, x);
+  x = __fmaf_rn(sgn * c.lo, d.hi, x);
+  x = __fmaf_rn(sgn * c.hi, d.lo, __fadd_rn(x, e2));
+  const float s = __fadd_rn(p1, p2);
+  const float bb = __fsub_rn(s, p1);
+  const float t = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bb)), __fsub_rn(p2, bb));
+  return df_renorm(df{s, __fadd_rn(t, x)});
+}
+// acc + a*b + sgn * c*d
+LGF_D df df_dot2_acc(df acc, df a, df b, df c, df d, float sgn) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  const float p2 = __fmul_rn(sgn * c.hi, d.hi);
+  const float e2 = __fmaf_rn(sgn * c.hi, d.hi, -p2);
+  float x = __fmaf_rn(a.lo, b.hi, e1);
+  x = __fmaf_rn(a.hi, b.lo, x);
+  x = __fmaf_rn(sgn * c.lo, d.hi, x);
+  x = __fmaf_rn(sgn * c.hi, d.lo, __fadd_rn(x, e2));
+  float s = __fadd_rn(acc.hi, p1);
+  float bb = __fsub_rn(s, acc.hi);
+  const float t1 = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p1, bb));
+  const float s2 = __fadd_rn(s, p2);
+  bb = __fsub_rn(s2, s);
+  const float t2 = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(p2, bb));
+  const float lo = __fadd_rn(__fadd_rn(acc.lo, x), __fadd_rn(t1, t2));
+  return df_renorm(df{s2, lo});
+}
+template <>
+LGF_D cx<df> cadd<df>(cx<df> a, cx<df> b) { return {df_add_lazy(a.re, b.re), df_add_lazy(a.im, b.im)}; }
+template <>
+LGF_D cx<df> csub<df>(cx<df> a, cx<df> b) { return {df_sub_lazy(a.re, b.re), df_sub_lazy(a.im, b.im)}; }
+template <>
+LGF_D cx<df> cmul<df>(cx<df> a, cx<df> b) {
+  return {df_dot2(a.re, b.re, a.im, b.im, -1.0f), df_dot2(a.re, b.im, a.im, b.re, 1.0f)};
+}
+template <>
+LGF_D cx<df> cnorm<df>(cx<df> a) { return {df_renorm(a.re), df_renorm(a.im)}; }
+LGF_D cx<df> cmac(cx<df> acc, cx<df> a, cx<df> b) {
+  return {df_dot2_acc(acc.re, a.re, b.re, a.im, b.im, -1.0f), df_dot2_acc(acc.im, a.re, b.im, a.im, b.re, 1.0f)};
+}
+
 // Twiddles W_64^j = cos(2 pi j / 64) - i sin(2 pi j / 64), j < 64, passed by value as a kernel
 // parameter (constant bank, broadcast to the warp).  Built on the host from sincospi in FP64.
 template <class R>
@@ -152,12 +234,14 @@ LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
       for (int j = 0; j < len / 2; ++j) {
         cx<R> u = x[i + j];
         cx<R> v = x[i + j + len / 2];
-        if (j != 0) v = v * twiddle<R, 64, INV>(tw, j * (64 / len));
-        x[i + j] = u + v;
-        x[i + j + len / 2] = u - v;
+        if (j != 0) v = cmul(v, twiddle<R, 64, INV>(tw, j * (64 / len)));
+        x[i + j] = cadd(u, v);
+        x[i + j + len / 2] = csub(u, v);
       }
     }
   }
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = cnorm(x[i]);
 }
 
 // ------------------------------------------------------------------ loads/stores of fields

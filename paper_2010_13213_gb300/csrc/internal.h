@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lgf.h"
@@ -86,6 +87,22 @@ struct PairOps {
                  const int4 *tgt_coords, int ncomp, int accumulate, cudaStream_t st);
 };
 
+// Kernel spectrum and twiddles of the block-index FFT mode for one box shape (box_spec.cu).
+struct BoxSpec {
+  int nb[3] = {0, 0, 0};
+  double *g64 = nullptr;  // [P^3 blocks][B^3] real spectrum, FP64
+  float *g32 = nullptr;
+  df *gdf = nullptr;
+  cx<double> *tw64[3] = {nullptr, nullptr, nullptr};  // W_Pc^n per axis, n < Pc
+  cx<float> *tw32[3] = {nullptr, nullptr, nullptr};
+  cx<df> *twdf[3] = {nullptr, nullptr, nullptr};
+  cx<double> bw64[3][32];  // W_P^n per axis, n < P (host copies for kernel parameters)
+  cx<float> bw32[3][32];
+  cx<df> bwdf[3][32];
+  size_t bytes = 0;
+  ~BoxSpec();
+};
+
 // Growable device buffer (never shrinks; freed with the owner).
 struct DevBuf {
   void *p = nullptr;
@@ -121,6 +138,10 @@ struct Workspace {
 
 }  // namespace lgf
 
+namespace lgf {
+int box_spectrum(lgf_table *t, const int nb[3], BoxSpec **out, cudaStream_t st);
+}
+
 struct lgf_table {
   int B = 0;
   int3 mo{0, 0, 0};  // max block offset per axis
@@ -136,4 +157,5 @@ struct lgf_table {
   void *sdf = nullptr;         // [noff][W] cx<df>
   std::mutex mu;
   std::map<void *, lgf::Workspace *> ws;  // keyed by stream
+  std::map<std::tuple<int, int, int>, lgf::BoxSpec *> box;  // block-index FFT spectra by box shape
 };

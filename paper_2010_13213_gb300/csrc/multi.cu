@@ -20,10 +20,14 @@
 #include <vector>
 
 #include "amr.cuh"
+#include "box_ops.cuh"
 #include "plan.h"
 #include "solver.h"
 
 namespace lgf {
+
+double box_cost(int B, const int nb[3]);
+double pair_cost(int B, double nsrc, double ntgt);
 
 // ------------------------------------------------------------------ plan cache (process-wide)
 static std::mutex g_plan_mu;
@@ -153,10 +157,32 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     maxSB = std::max<int64_t>(maxSB, (int64_t)L.SB.size());
     maxT = std::max<int64_t>(maxT, (int64_t)L.nTall);
   }
+  // per level: pair or block-index FFT (box) evaluation of the block-pair sums
+  std::vector<int> use_box(K, 0);
+  int64_t maxbox = 0;
+  for (int k = 0; k < K; ++k) {
+    const LevelPlan &L = P->L[k];
+    if (!L.box_ok || L.Tall.empty()) continue;
+    if (o.mac_mode == LGF_MAC_BOX) {
+      use_box[k] = 1;
+    } else if (o.mac_mode == LGF_MAC_AUTO) {
+      const bool packAB = !L.Tpsi.empty() || !L.SB.empty();
+      const double cb = box_cost(B, L.box_nb) * (packAB ? 2.0 : 1.0);
+      const double cp = pair_cost(B, (double)L.SA.size(), (double)L.nTall) +
+                        pair_cost(B, (double)L.SB.size(), (double)L.Tphi.size());
+      use_box[k] = cb < cp;
+    }
+    if (use_box[k]) maxbox = std::max<int64_t>(maxbox, 8 * L.nbox * B3);
+  }
+  if (o.mac_mode == LGF_MAC_BOX)
+    for (int k = 0; k < K; ++k)
+      if (!use_box[k] && !P->L[k].Tall.empty())
+        return set_error(LGF_E_UNSUPPORTED, "BOX mode needs 1..16 blocks per axis on level %d", k);
   Workspace *ws = workspace_for(t, st);
   const size_t field = sizeof(R) * (size_t)ncomp * maxBL * B3;
-  if ((rc = ws->buf[0].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxSA, 1) * W)) ||
-      (rc = ws->buf[1].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxT, 1) * W)) ||
+  const size_t ybytes = sizeof(cx<R>) * (size_t)maxbox;
+  if ((rc = ws->buf[0].reserve(std::max(ybytes, sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxSA, 1) * W))) ||
+      (rc = ws->buf[1].reserve(std::max(ybytes, sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxT, 1) * W))) ||
       (rc = ws->buf[3].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxSB, 1) * W)) ||
       (rc = ws->buf[4].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[5].reserve(field)) ||
       (rc = ws->buf[6].reserve(field)) || (rc = ws->buf[7].reserve(sizeof(R) * (size_t)Foff[K])) ||
@@ -205,6 +231,61 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
                                                      psi_prev, ccs, k > 0);
       LGF_LAUNCH_CHECK("correct");
       tm.mark(PH_CORRECT);
+    }
+    if (use_box[k]) {
+      BoxSpec *S = nullptr;
+      if ((rc = box_spectrum(t, L.box_nb, &S, st))) return rc;
+      const int32_t *gA = L.d_box, *gB = gA + L.nbox, *sPsi = gB + L.nbox, *sPhi = sPsi + L.nbox;
+      const double scale = L.h * L.h / (8.0 * L.nbox * (double)B3);
+      const bool packAB = nPsi > 0 || nSB > 0;
+      const R *cadd = k > 0 ? c : nullptr;
+      cx<R> *Y0 = (cx<R> *)ws->buf[0].p, *Y1 = (cx<R> *)ws->buf[1].p;
+      if (packAB) {
+        // z = A + i (A + B): real part -> psi_k on the psi targets, imaginary part -> phi on Omega_k
+        for (int cc = 0; cc < ncomp; ++cc) {
+          InSpec in[3];
+          int ns = 0;
+          if (nSA) {
+            in[ns++] = InSpec{gA, A + cc * cs[k], nullptr, 2, 0, 0};
+            in[ns++] = InSpec{gA, A + cc * cs[k], nullptr, 2, 0, 1};
+          }
+          if (nSB) in[ns++] = InSpec{gB, Fall + Foff[k] + cc * cs[k], L.d_cellmask, 2, CB_COV, 1};
+          OutSpec<R> ore{nPsi ? sPsi : nullptr, nullptr, Psi + Foff[k], cadd ? cadd + cc * cs[k] : nullptr, nullptr,
+                         cc * cs[k], 2, 0};
+          OutSpec<R> oim{nPhi ? sPhi : nullptr, nullptr, phi, cadd ? cadd + cc * cs[k] : nullptr, L.d_cellmask,
+                         cc * ucs + L.user_off * B3, dtype, CB_OM};
+          if (ns == 0) continue;
+          if ((rc = BoxOps<R>::convolve(B, S, ns, in, ore, oim, scale, Y0, Y1, st, o.timing ? phase_mark_cb : nullptr,
+                                        &tm)))
+            return rc;
+          launches += 7;
+        }
+      } else {
+        // finest level without psi targets: two components per complex field, both to phi
+        for (int c0 = 0; c0 < ncomp; c0 += 2) {
+          const int c1 = c0 + 1;
+          InSpec in[2];
+          int ns = 0;
+          in[ns++] = InSpec{gA, A + c0 * cs[k], nullptr, 2, 0, 0};
+          if (c1 < ncomp) in[ns++] = InSpec{gA, A + c1 * cs[k], nullptr, 2, 0, 1};
+          OutSpec<R> ore{sPhi, nullptr, phi, cadd ? cadd + c0 * cs[k] : nullptr, L.d_cellmask,
+                         c0 * ucs + L.user_off * B3, dtype, CB_OM};
+          OutSpec<R> oim{};
+          if (c1 < ncomp)
+            oim = OutSpec<R>{sPhi, nullptr, phi, cadd ? cadd + c1 * cs[k] : nullptr, L.d_cellmask,
+                             c1 * ucs + L.user_off * B3, dtype, CB_OM};
+          if ((rc = BoxOps<R>::convolve(B, S, ns, in, ore, oim, scale, Y0, Y1, st, o.timing ? phase_mark_cb : nullptr,
+                                        &tm)))
+            return rc;
+          launches += 7;
+        }
+      }
+      target_cells += L.n_omega;
+      nsrc_total += nSA + nSB;
+      ntgt_total += nT;
+      continue;
+    }
+    if (nSA) {
       if ((rc = PairOps<R>::forward(B, A, 2, cs[k], lists + L.off_SA, nSA, ncomp, FA, nullptr, 0, st))) return rc;
       ++launches;
     }
@@ -288,6 +369,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     rep->scratch_bytes = (int64_t)ws->total() + (int64_t)P->device_bytes;
     rep->kernel_launches = launches;
     rep->mac_mode_used = LGF_MAC_PAIR;
+    for (int k = 0; k < K; ++k)
+      if (use_box[k]) rep->mac_mode_used = LGF_MAC_BOX;
   }
   if (o.residual && o.residual_tol > 0 && resid > o.residual_tol)
     return set_error(LGF_E_PRECISION, "FP64 residual %.3e exceeds the tolerance %.3e", resid, o.residual_tol);

@@ -29,7 +29,7 @@ LGF_D void dft_pad_fwd(const Tw64<R> &tw, Load load, Put put) {
 #pragma unroll
   for (int j = 0; j < B; ++j) {
     x[j] = load(j);
-    if (j) x[j] = x[j] * twiddle<R, 2 * B, false>(tw, j);
+    if (j) x[j] = cmul(x[j], twiddle<R, 2 * B, false>(tw, j));
   }
   fft_reg<R, B, false>(x, tw);
 #pragma unroll
@@ -52,7 +52,7 @@ LGF_D void dft_window_inv(const Tw64<R> &tw, Load load, Put put, Add add) {
 #pragma unroll
   for (int j = 0; j < B; ++j) {
     cx<R> v = x[j];
-    if (j) v = v * twiddle<R, 2 * B, true>(tw, j);
+    if (j) v = cmul(v, twiddle<R, 2 * B, true>(tw, j));
     add(j, v);
   }
 }
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(128) k_mac_pair(const cx<R> *__restrict__ F, i
                       (tc[i].x - sc.x + mo.x);
       const cx<R> g = Gh[(int64_t)idx * W + w];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[i][c] = acc[i][c] + g * fv[c];
+      for (int c = 0; c < NC; ++c) acc[i][c] = cmac(acc[i][c], g, fv[c]);
     }
   }
 #pragma unroll

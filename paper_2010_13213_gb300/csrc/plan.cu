@@ -86,6 +86,7 @@ Plan::~Plan() {
     cudaFree(l.d_lists);
     cudaFree(l.d_phi_oct);
     cudaFree(l.d_user_of);
+    cudaFree(l.d_box);
   }
 }
 
@@ -338,6 +339,44 @@ int build_plan(const lgf_mesh *m, const int *heat_radii, Plan **out) {
     lists.insert(lists.end(), L.Tpsi.begin(), L.Tpsi.end());
     L.off_HB = (int)lists.size();
     lists.insert(lists.end(), L.HB.begin(), L.HB.end());
+    // block-index FFT box
+    {
+      int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+      auto acc = [&](const std::vector<int32_t> &lst) {
+        for (int b : lst) {
+          const int v[3] = {L.BL[b].x, L.BL[b].y, L.BL[b].z};
+          for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], v[a]), hi[a] = std::max(hi[a], v[a]);
+        }
+      };
+      acc(L.SA);
+      acc(L.SB);
+      acc(L.Tall);
+      L.box_ok = !L.Tall.empty();
+      for (int a = 0; a < 3 && L.box_ok; ++a) {
+        L.box_lo[a] = lo[a];
+        L.box_nb[a] = hi[a] - lo[a] + 1;
+        if (L.box_nb[a] < 1 || L.box_nb[a] > 16) L.box_ok = false;
+      }
+      if (L.box_ok) {
+        L.nbox = (int64_t)L.box_nb[0] * L.box_nb[1] * L.box_nb[2];
+        std::vector<int32_t> maps(4 * L.nbox, -1);
+        auto put = [&](const std::vector<int32_t> &lst, int which) {
+          for (int b : lst) {
+            const int x = L.BL[b].x - lo[0], y = L.BL[b].y - lo[1], z = L.BL[b].z - lo[2];
+            maps[which * L.nbox + ((int64_t)z * L.box_nb[1] + y) * L.box_nb[0] + x] = b;
+          }
+        };
+        put(L.SA, 0);
+        put(L.SB, 1);
+        put(L.Tpsi, 2);
+        put(L.Tphi, 3);
+        int rc2 = upload(&L.d_box, maps, &P->device_bytes);
+        if (rc2) {
+          delete P;
+          return rc2;
+        }
+      }
+    }
     std::vector<int32_t> user_of(nBL, -1);
     for (int i = 0; i < L.nU; ++i) user_of[i] = (int32_t)(L.user_off + i);
     int rc;

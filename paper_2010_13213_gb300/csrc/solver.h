@@ -15,8 +15,8 @@ int solve_heat(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *
 struct PhaseTimer {
   bool on = false;
   cudaStream_t st = nullptr;
-  cudaEvent_t ev[32];
-  int phase_of[32];
+  cudaEvent_t ev[160];
+  int phase_of[160];
   int n = 0;
   void start(bool enable, cudaStream_t s) {
     on = enable;
@@ -25,7 +25,7 @@ struct PhaseTimer {
     if (on) mark(-1);
   }
   void mark(int phase) {
-    if (!on || n >= 32) return;
+    if (!on || n >= 160) return;
     cudaEventCreate(&ev[n]);
     cudaEventRecord(ev[n], st);
     phase_of[n] = phase;
@@ -47,6 +47,8 @@ struct PhaseTimer {
     n = 0;
   }
 };
+
+inline void phase_mark_cb(void *ctx, int phase) { ((PhaseTimer *)ctx)->mark(phase); }
 
 enum Phase { PH_RESTRICT = 0, PH_CORRECT, PH_FORWARD, PH_MAC, PH_INVERSE, PH_INTERP, PH_RESIDUAL, PH_HEAT };
 
