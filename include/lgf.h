@@ -172,6 +172,44 @@ int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f
                    void *g_dev, int32_t dtype, double alpha_finest, const lgf_solve_opts *opts,
                    lgf_report *rep, void *cuda_stream);
 
+/* ---- batches: many independent instances solved as one unit, capturable into a CUDA graph */
+typedef struct lgf_batch lgf_batch; /* opaque */
+
+/*
+ * lgf_batch_create -- plan a batch of `ninst` independent composite-mesh problems sharing table `t`
+ * (the right-hand sides of the stages of a half-explicit Runge-Kutta step, Sec. 2.4: one Poisson
+ * solve, Eq. (eq:projection-1), and one integrating-factor apply, Eq. (eq:projection-2), per instance).
+ *   meshes   : host [ninst]; copied (the caller's arrays may be released after the call).  block_role
+ *              is ignored; every mesh's block size must equal the table's.
+ *   ncomp    : components per instance; dtype: LGF_F64 / LGF_F32 storage of every field.
+ *   alpha    : host [ninst] integrating-factor argument kappa*dt/h_finest^2 per instance, or NULL (0).
+ *   opts     : precision / mac_mode for every solve (residual and timing are forced off); may be NULL.
+ *   nstreams : 1..64 internal streams; instances are dealt longest-first to the least-loaded stream.
+ */
+int lgf_batch_create(lgf_batch **out, lgf_table *t, int32_t ninst, const lgf_mesh *meshes, int32_t ncomp,
+                     int32_t dtype, const double *alpha, const lgf_solve_opts *opts, int32_t nstreams);
+int lgf_batch_destroy(lgf_batch *b);
+
+/*
+ * lgf_batch_stage -- for every instance i: phi_dev[i] = L^{-1} f_dev[i] and, when g_dev is non-NULL,
+ * g_dev[i] = FIF-AMR heat apply of f_dev[i].  Device arrays laid out as for lgf_poisson_solve.
+ * Work runs on the batch's streams, forked from and joined back into cuda_stream (asynchronous).
+ */
+int lgf_batch_stage(lgf_batch *b, const void *const *f_dev, void *const *phi_dev, void *const *g_dev,
+                    void *cuda_stream);
+
+/*
+ * lgf_batch_graph_create -- run two eager stages (building every plan, spectrum and workspace), then
+ * capture `nstages` chained stages into a CUDA graph: stage 0 reads f and writes g, stage s >= 1 reads
+ * the previous stage's heat output (g or tmp, alternating) and writes the other; every stage writes
+ * phi.  cuda_stream must be a non-default stream.  Synchronises.  lgf_batch_graph_launch replays it
+ * with one cudaGraphLaunch; lgf_batch_graph_nodes returns its node count.
+ */
+int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_dev, void *const *phi_dev,
+                           void *const *g_dev, void *const *tmp_dev, void *cuda_stream);
+int lgf_batch_graph_launch(lgf_batch *b, void *cuda_stream);
+int lgf_batch_graph_nodes(const lgf_batch *b, int64_t *nodes);
+
 /*
  * lgf_poisson_solve_static -- single-level solve (pair mode) that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that must not allocate during a

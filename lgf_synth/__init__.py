@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "random_box", "ring_vorticity", "two_ring_vorticity", "bump_streamfunction",
     "box_blocks", "box_to_blocks", "blocks_to_box", "single_level_random", "single_level_ring",
-    "three_level_ring", "two_ring_single_level", "batch_instances", "blocks_with_support",
+    "three_level_ring", "two_ring_single_level", "batch_instances", "blocks_with_support", "ring_instance",
 ]
 
 
@@ -192,6 +192,50 @@ def three_level_ring(R=1.0, sigma=0.2, B=16, thresholds=(1e-3, 1e-2), n_ext=16, 
         f.append(box_to_blocks(box, blocks[k], B))
     mesh = dict(B=B, h0=hs[0], n_ext=n_ext, levels=[np.ascontiguousarray(b) for b in blocks])
     return mesh, f
+
+
+def ring_instance(p, B=16, n_ext=16, thresholds=(1e-3, 1e-2), drop=1e-6):
+    """Composite mesh of one batch instance (dict from ``batch_instances``): K = p["levels"] levels,
+    finest spacing p["h_fine"], finest box p["nxy"]^2 x p["nz"] cells centred on the ring.  Level 0 covers
+    the box at its own spacing (rounded up to blocks) dilated by one block; for K = 3 level 1 holds the
+    blocks with |omega| > thresholds[0] max plus the parents of level 2; the finest level (K >= 2) holds
+    the blocks with |omega| > thresholds[1] max; for K = 1 the single level is the box, with source
+    blocks those reaching drop * max.  Returns (mesh, f_levels, roles or None)."""
+    K, R, sig = p["levels"], p["R"], p["sigma"]
+    hf = p["h_fine"]
+    hs = [hf * 2 ** (K - 1 - k) for k in range(K)]
+    fine_n = (p["nxy"], p["nxy"], p["nz"])
+    scale = 2 ** (K - 1)
+    n0 = tuple(int(math.ceil(n / scale / B)) * B + (2 * B if K > 1 else 0) for n in fine_n)
+    origin = (-n0[0] * hs[0] / 2, -n0[1] * hs[0] / 2, -n0[2] * hs[0] / 2)
+
+    def field(nx, ny, nz, h):
+        return ring_vorticity(nx, ny, nz, h, R, sig, origin=origin)
+
+    n_lev = [tuple(n * 2 ** k for n in n0) for k in range(K)]
+    vmax = np.sqrt((field(*n_lev[K - 1], hs[K - 1]) ** 2).sum(0)).max()
+    blocks = [box_blocks((n0[2], n0[1], n0[0]), B)]
+    roles = None
+    if K == 1:
+        box = field(*n0, hs[0])
+        src = {tuple(b) for b in blocks_with_support(box, B, drop)}
+        roles = np.array([2 + (1 if tuple(b) in src else 0) for b in blocks[0]], np.uint8)
+    if K >= 2:
+        fine = _level_blocks_over(field_fn=lambda nx, ny, nz, h, o: field(nx, ny, nz, h), nxyz=n_lev[K - 1],
+                                  h=hs[K - 1], origin=origin, B=B, rel=thresholds[1], vmax=vmax)
+        levels_mid = []
+        if K == 3:
+            mid = _level_blocks_over(field_fn=lambda nx, ny, nz, h, o: field(nx, ny, nz, h), nxyz=n_lev[1], h=hs[1],
+                                     origin=origin, B=B, rel=thresholds[0], vmax=vmax)
+            parents = np.unique((fine * B // 2) // B, axis=0)
+            levels_mid = [np.unique(np.concatenate([mid, parents]), axis=0).astype(np.int32)]
+        blocks += levels_mid + [fine]
+    f = []
+    for k in range(K):
+        nx, ny, nz = n_lev[k]
+        f.append(box_to_blocks(field(nx, ny, nz, hs[k]), blocks[k], B))
+    mesh = dict(B=B, h0=hs[0], n_ext=n_ext, levels=[np.ascontiguousarray(b, dtype=np.int32) for b in blocks])
+    return mesh, f, roles
 
 
 def batch_instances(n=64, seed0=1000, B=16):

@@ -1,0 +1,210 @@
+// batch.cu -- many independent solves as one unit of work, and its CUDA-graph capture.
+//
+// A batch holds N instances (each its own composite mesh, sharing the LGF table and its block size)
+// and S internal streams.  A stage runs, for every instance i,
+//     phi_i = L^{-1} f_i          (FLGF-AMR, Sec. 3.4)
+//     g_i   = E_{alpha_i} * f_i   (FIF-AMR, Sec. 3.5; alpha_i for the finest level)
+// -- the two solves a half-explicit Runge-Kutta stage needs (Sec. 2.4, Eqs. (eq:projection-1) and
+// (eq:projection-2)).  Instances are dealt to the streams longest-first (a host work queue in LPT
+// order), each stream runs its instances back to back, and the streams fork from / join into the
+// caller's stream through events, so a stage is capturable: lgf_batch_graph_create captures a chain
+// of stages (stage s reads the g written by stage s-1) into one CUDA graph, replayed by
+// lgf_batch_graph_launch with a single launch.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+#include "solver.h"
+
+struct lgf_batch {
+  lgf_table *t = nullptr;
+  int n = 0, ncomp = 1, dtype = 0, nstreams = 1;
+  lgf_solve_opts opts{};
+  std::vector<int32_t> nb_all, ijk_all;           // concatenated mesh arrays
+  std::vector<lgf_mesh> mesh;                      // per instance (pointers into the arrays above)
+  std::vector<std::vector<int32_t>> nbk, ijk;      // per instance owned copies
+  std::vector<double> alpha;
+  std::vector<double> cost;
+  std::vector<std::vector<int>> by_stream;         // instance lists per stream
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_stages = 0;
+  bool warmed = false;
+};
+
+namespace lgf {
+double box_cost(int B, const int nb[3]);
+}
+
+using namespace lgf;
+
+static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, void *const *g, cudaStream_t st) {
+  if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return set_error(LGF_E_CUDA, "batch fork event failed");
+  for (int s = 0; s < b->nstreams; ++s) {
+    cudaStream_t ss = b->streams[s];
+    cudaStreamWaitEvent(ss, b->ev_fork, 0);
+    for (int i : b->by_stream[s]) {
+      int rc = lgf_poisson_solve(b->t, &b->mesh[i], b->ncomp, f[i], phi[i], b->dtype, &b->opts, nullptr, ss);
+      if (rc) return rc;
+      if (g && g[i]) {
+        rc = lgf_heat_apply(b->t, &b->mesh[i], b->ncomp, f[i], g[i], b->dtype, b->alpha[i], &b->opts, nullptr, ss);
+        if (rc) return rc;
+      }
+    }
+    cudaEventRecord(b->ev_join[s], ss);
+    cudaStreamWaitEvent(st, b->ev_join[s], 0);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "batch stage: %s", cudaGetErrorString(e));
+}
+
+extern "C" {
+
+int lgf_batch_create(lgf_batch **out, lgf_table *t, int32_t ninst, const lgf_mesh *meshes, int32_t ncomp,
+                     int32_t dtype, const double *alpha, const lgf_solve_opts *opts, int32_t nstreams) {
+  if (!out || !t || !meshes || ninst < 1 || ncomp < 1) return set_error(LGF_E_INVALID_ARG, "bad batch arguments");
+  if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
+  if (nstreams < 1 || nstreams > 64) return set_error(LGF_E_INVALID_ARG, "nstreams %d out of [1, 64]", nstreams);
+  *out = nullptr;
+  lgf_batch *b = new lgf_batch();
+  b->t = t;
+  b->n = ninst;
+  b->ncomp = ncomp;
+  b->dtype = dtype;
+  b->nstreams = std::min<int>(nstreams, ninst);
+  if (opts) b->opts = *opts;
+  b->opts.residual = 0;  // stages must stay free of synchronisation
+  b->opts.timing = 0;
+  b->mesh.resize(ninst);
+  b->nbk.resize(ninst);
+  b->ijk.resize(ninst);
+  b->alpha.assign(ninst, 0.0);
+  b->cost.assign(ninst, 0.0);
+  for (int i = 0; i < ninst; ++i) {
+    const lgf_mesh &m = meshes[i];
+    if (!m.nblocks || !m.block_ijk || m.nlevels < 1 || m.block != t->B) {
+      delete b;
+      return set_error(LGF_E_MESH, "instance %d: invalid mesh", i);
+    }
+    int64_t tot = 0;
+    for (int k = 0; k < m.nlevels; ++k) tot += m.nblocks[k];
+    b->nbk[i].assign(m.nblocks, m.nblocks + m.nlevels);
+    b->ijk[i].assign(m.block_ijk, m.block_ijk + 3 * tot);
+    b->mesh[i] = m;
+    b->mesh[i].nblocks = b->nbk[i].data();
+    b->mesh[i].block_ijk = b->ijk[i].data();
+    b->mesh[i].block_role = nullptr;
+    b->alpha[i] = alpha ? alpha[i] : 0.0;
+    b->cost[i] = (double)tot;
+  }
+  // longest-processing-time-first assignment of instances to streams
+  std::vector<int> order(ninst);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return b->cost[a] > b->cost[c]; });
+  b->by_stream.assign(b->nstreams, {});
+  std::vector<double> load(b->nstreams, 0.0);
+  for (int i : order) {
+    const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->by_stream[s].push_back(i);
+    load[s] += b->cost[i];
+  }
+  b->streams.resize(b->nstreams);
+  b->ev_join.resize(b->nstreams);
+  for (int s = 0; s < b->nstreams; ++s) {
+    if (cudaStreamCreateWithFlags(&b->streams[s], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join[s], cudaEventDisableTiming) != cudaSuccess) {
+      delete b;
+      return set_error(LGF_E_CUDA, "batch stream creation failed");
+    }
+  }
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return set_error(LGF_E_CUDA, "batch event creation failed");
+  }
+  *out = b;
+  return LGF_OK;
+}
+
+int lgf_batch_destroy(lgf_batch *b) {
+  if (!b) return LGF_OK;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->ev_join) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  delete b;
+  return LGF_OK;
+}
+
+int lgf_batch_stage(lgf_batch *b, const void *const *f_dev, void *const *phi_dev, void *const *g_dev,
+                    void *cuda_stream) {
+  if (!b || !f_dev || !phi_dev) return set_error(LGF_E_INVALID_ARG, "NULL argument");
+  int rc = batch_stage(b, f_dev, phi_dev, g_dev, (cudaStream_t)cuda_stream);
+  if (!rc) b->warmed = true;
+  return rc;
+}
+
+int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_dev, void *const *phi_dev,
+                           void *const *g_dev, void *const *tmp_dev, void *cuda_stream) {
+  if (!b || !f_dev || !phi_dev || !g_dev || nstages < 1) return set_error(LGF_E_INVALID_ARG, "NULL argument");
+  if (nstages > 1 && !tmp_dev) return set_error(LGF_E_INVALID_ARG, "chained stages need tmp buffers");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // an eager stage creates every plan, spectrum and workspace the captured stages will use
+  std::vector<const void *> src(b->n);
+  std::vector<void *> dst(b->n);
+  for (int i = 0; i < b->n; ++i) src[i] = f_dev[i], dst[i] = g_dev[i];
+  int rc = batch_stage(b, src.data(), phi_dev, dst.data(), st);
+  if (rc) return rc;
+  if (nstages > 1) {
+    for (int i = 0; i < b->n; ++i) src[i] = g_dev[i], dst[i] = tmp_dev[i];
+    if ((rc = batch_stage(b, src.data(), phi_dev, dst.data(), st))) return rc;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return set_error(LGF_E_CUDA, "batch warm-up failed");
+  if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
+  if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return set_error(LGF_E_CUDA, "stream capture could not begin (use a non-default stream)");
+  for (int s = 0; s < nstages && !rc; ++s) {
+    for (int i = 0; i < b->n; ++i) {
+      if (s == 0) src[i] = f_dev[i], dst[i] = g_dev[i];
+      else if (s % 2 == 1) src[i] = g_dev[i], dst[i] = tmp_dev[i];
+      else src[i] = tmp_dev[i], dst[i] = g_dev[i];
+    }
+    rc = batch_stage(b, src.data(), phi_dev, dst.data(), st);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess || !graph) return set_error(LGF_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return set_error(LGF_E_CUDA, "graph instantiation failed");
+  }
+  b->graph = graph;
+  b->graph_stages = nstages;
+  return LGF_OK;
+}
+
+int lgf_batch_graph_launch(lgf_batch *b, void *cuda_stream) {
+  if (!b || !b->exec) return set_error(LGF_E_INVALID_ARG, "no captured graph");
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "graph launch: %s", cudaGetErrorString(e));
+}
+
+int lgf_batch_graph_nodes(const lgf_batch *b, int64_t *nodes) {
+  if (!b || !b->graph || !nodes) return set_error(LGF_E_INVALID_ARG, "no captured graph");
+  size_t n = 0;
+  if (cudaGraphGetNodes(b->graph, nullptr, &n) != cudaSuccess) return set_error(LGF_E_CUDA, "graph query failed");
+  *nodes = (int64_t)n;
+  return LGF_OK;
+}
+
+}  // extern "C"

@@ -65,7 +65,7 @@ int get_plan(const lgf_mesh *m, const int *radii, Plan **out) {
   int rc = build_plan(m, radii, &P);
   if (rc) return rc;
   g_plans.emplace_front(key, P);
-  while (g_plans.size() > 32) {
+  while (g_plans.size() > 1024) {
     delete g_plans.back().second;  // cudaFree inside orders against in-flight work
     g_plans.pop_back();
   }
@@ -73,7 +73,8 @@ int get_plan(const lgf_mesh *m, const int *radii, Plan **out) {
   return LGF_OK;
 }
 
-static LevelDev level_dev(const Plan *P, int k) {
+// Device view of level k; the spacing comes from the caller's mesh (plans are keyed by geometry only).
+static LevelDev level_dev(const Plan *P, int k, double h0) {
   const LevelPlan &L = P->L[k];
   LevelDev d;
   d.map = L.d_map;
@@ -84,7 +85,7 @@ static LevelDev level_dev(const Plan *P, int k) {
   int s = 0;
   while ((1 << s) < P->B) ++s;
   d.shift = s;
-  d.h = L.h;
+  d.h = h0 / (double)(1 << k);
   return d;
 }
 
@@ -198,7 +199,7 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
   // 1. cumulative coarsening
   for (int k = K - 1; k >= 0; --k) {
     const LevelPlan &L = P->L[k];
-    const LevelDev Ld = level_dev(P, k);
+    const LevelDev Ld = level_dev(P, k, m->h0);
     k_restrict<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, f, dtype, ucs, L.user_off, Fall + Foff[k], cs[k]);
     LGF_LAUNCH_CHECK("restrict");
     if (k + 1 < K) {
@@ -213,8 +214,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
   // 2. coarse to fine
   for (int k = 0; k < K; ++k) {
     const LevelPlan &L = P->L[k];
-    const LevelDev Ld = level_dev(P, k);
-    const LevelDev Lc = k > 0 ? level_dev(P, k - 1) : Ld;
+    const LevelDev Ld = level_dev(P, k, m->h0);
+    const LevelDev Lc = k > 0 ? level_dev(P, k - 1, m->h0) : Ld;
     const int64_t ccs = k > 0 ? cs[k - 1] : 0;
     const R *psi_prev = k > 0 ? Psi + Foff[k - 1] : nullptr;
     R *psi_cur = Psi + Foff[k];
@@ -236,7 +237,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       BoxSpec *S = nullptr;
       if ((rc = box_spectrum(t, L.box_nb, &S, st))) return rc;
       const int32_t *gA = L.d_box, *gB = gA + L.nbox, *sPsi = gB + L.nbox, *sPhi = sPsi + L.nbox;
-      const double scale = L.h * L.h / (8.0 * L.nbox * (double)B3);
+      const double hk = m->h0 / (double)(1 << k);
+      const double scale = hk * hk / (8.0 * L.nbox * (double)B3);
       const bool packAB = nPsi > 0 || nSB > 0;
       const R *cadd = k > 0 ? c : nullptr;
       cx<R> *Y0 = (cx<R> *)ws->buf[0].p, *Y1 = (cx<R> *)ws->buf[1].p;
@@ -296,7 +298,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       ++launches;
     }
     tm.mark(PH_FORWARD);
-    const double scale = L.h * L.h / (double)((2 * B) * (2 * B) * (2 * B));
+    const double hk = m->h0 / (double)(1 << k);
+    const double scale = hk * hk / (double)((2 * B) * (2 * B) * (2 * B));
     const int64_t pcs = (int64_t)nT * W;
     if (nSA) {
       if ((rc = PairOps<R>::mac(B, FA, nSA, (int64_t)nSA * W, lists + L.off_SA, L.d_BL, Gh, t->mo, Phi, nT, pcs,
@@ -341,8 +344,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     for (int k = 0; k < K; ++k) {
       const LevelPlan &L = P->L[k];
       if (L.Tphi.empty()) continue;
-      const LevelDev Ld = level_dev(P, k);
-      const LevelDev Lc = k > 0 ? level_dev(P, k - 1) : Ld;
+      const LevelDev Ld = level_dev(P, k, m->h0);
+      const LevelDev Lc = k > 0 ? level_dev(P, k - 1, m->h0) : Ld;
       k_residual<R><<<dim3((unsigned)L.Tphi.size(), ncomp), 256, 0, st>>>(
           Ld, L.d_BL, L.d_lists + L.off_Tall, phi, dtype, ucs, Fall + Foff[k], cs[k], Lc,
           k > 0 ? Psi + Foff[k - 1] : nullptr, k > 0 ? cs[k - 1] : 0, k > 0, racc + 2 * k);
@@ -465,7 +468,7 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
   tm.start(o.timing != 0, st);
   for (int k = K - 1; k >= 0; --k) {
     const LevelPlan &L = P->L[k];
-    const LevelDev Ld = level_dev(P, k);
+    const LevelDev Ld = level_dev(P, k, m->h0);
     k_restrict<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, f, dtype, ucs, L.user_off, Fall + Foff[k], cs[k]);
     LGF_LAUNCH_CHECK("restrict");
     if (k + 1 < K) {
@@ -479,8 +482,8 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
   int64_t target_cells = 0;
   for (int k = 0; k < K; ++k) {
     const LevelPlan &L = P->L[k];
-    const LevelDev Ld = level_dev(P, k);
-    const LevelDev Lc = k > 0 ? level_dev(P, k - 1) : Ld;
+    const LevelDev Ld = level_dev(P, k, m->h0);
+    const LevelDev Lc = k > 0 ? level_dev(P, k - 1, m->h0) : Ld;
     const int nHB = (int)L.HB.size();
     const int32_t *HB = L.d_lists + L.off_HB;
     const size_t bytes = sizeof(R) * (size_t)ncomp * L.BL.size() * B3;

@@ -120,7 +120,6 @@ int build_plan(const lgf_mesh *m, const int *heat_radii, Plan **out) {
   for (int k = 0; k < K; ++k) {
     LevelPlan &L = P->L[k];
     L.k = k;
-    L.h = m->h0 / (double)(1 << k);
     L.user_off = off;
     L.nU = m->nblocks[k];
     L.heat_r = heat_radii ? heat_radii[k] : 0;

@@ -24,7 +24,6 @@ enum CellBits : uint8_t { CB_OM = 1, CB_EX = 2, CB_COV = 4 };
 
 struct LevelPlan {
   int k = 0;
-  double h = 0.0;
   int64_t user_off = 0;            // first block of this level in the caller's arrays
   int nU = 0;                      // caller blocks of this level
   // internal block set BL (caller blocks first, in caller order, then added blocks)

@@ -81,10 +81,19 @@ def load():
                                        c_double, POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
         lib.lgf_poisson_solve_static.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p,
                                                  c_int32, c_int32, c_void_p]
+        PP = POINTER(c_void_p)
+        lib.lgf_batch_create.argtypes = [POINTER(c_void_p), c_void_p, c_int32, POINTER(lgf_mesh), c_int32, c_int32,
+                                         POINTER(c_double), POINTER(lgf_solve_opts), c_int32]
+        lib.lgf_batch_destroy.argtypes = [c_void_p]
+        lib.lgf_batch_stage.argtypes = [c_void_p, PP, PP, PP, c_void_p]
+        lib.lgf_batch_graph_create.argtypes = [c_void_p, c_int32, PP, PP, PP, PP, c_void_p]
+        lib.lgf_batch_graph_launch.argtypes = [c_void_p, c_void_p]
+        lib.lgf_batch_graph_nodes.argtypes = [c_void_p, POINTER(c_int64)]
         lib.lgf_last_error.restype = c_char_p
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
-                     "lgf_heat_apply", "lgf_poisson_solve_static"):
+                     "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_batch_create", "lgf_batch_destroy",
+                     "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes"):
             getattr(lib, name).restype = c_int32
         _LIB = lib
     return _LIB
@@ -170,6 +179,57 @@ def lgf_poisson_solve_static(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev:
     _check(load().lgf_poisson_solve_static(c_void_p(table), ctypes.byref(mesh.c), int(ncomp), c_void_p(f_dev),
                                            c_void_p(phi_dev), int(dtype), int(precision),
                                            c_void_p(cuda_stream or None)))
+
+
+def _ptrs(lst):
+    arr = (c_void_p * len(lst))(*[c_void_p(int(p)) if p else None for p in lst])
+    return ctypes.cast(arr, POINTER(c_void_p)), arr
+
+
+class Batch:
+    """Owns an ``lgf_batch`` and the host meshes behind it."""
+
+    def __init__(self, table, meshes, ncomp: int, dtype: int = LGF_F64, alpha=None, opts=None, nstreams: int = 8):
+        self.meshes = list(meshes)
+        carr = (lgf_mesh * len(self.meshes))(*[m.c for m in self.meshes])
+        al = None if alpha is None else (c_double * len(self.meshes))(*[float(a) for a in alpha])
+        h = c_void_p()
+        _check(load().lgf_batch_create(ctypes.byref(h), c_void_p(table), len(self.meshes), carr, int(ncomp),
+                                       int(dtype), al, ctypes.byref(opts) if opts is not None else None,
+                                       int(nstreams)))
+        self.h = h.value
+
+    def stage(self, f_ptrs, phi_ptrs, g_ptrs=None, cuda_stream: int = 0):
+        f, _a = _ptrs(f_ptrs)
+        p, _b = _ptrs(phi_ptrs)
+        g, _c = _ptrs(g_ptrs) if g_ptrs is not None else (None, None)
+        _check(load().lgf_batch_stage(c_void_p(self.h), f, p, g, c_void_p(cuda_stream or None)))
+
+    def graph_create(self, nstages, f_ptrs, phi_ptrs, g_ptrs, tmp_ptrs, cuda_stream: int):
+        f, _a = _ptrs(f_ptrs)
+        p, _b = _ptrs(phi_ptrs)
+        g, _c = _ptrs(g_ptrs)
+        t, _d = _ptrs(tmp_ptrs) if tmp_ptrs is not None else (None, None)
+        _check(load().lgf_batch_graph_create(c_void_p(self.h), int(nstages), f, p, g, t, c_void_p(cuda_stream)))
+
+    def graph_launch(self, cuda_stream: int):
+        _check(load().lgf_batch_graph_launch(c_void_p(self.h), c_void_p(cuda_stream)))
+
+    def graph_nodes(self) -> int:
+        n = c_int64()
+        _check(load().lgf_batch_graph_nodes(c_void_p(self.h), ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if self.h:
+            load().lgf_batch_destroy(c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 make_opts = _opts

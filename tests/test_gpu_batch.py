@@ -1,0 +1,140 @@
+"""GPU tests of the batched stage (lgf_batch_*): uneven ring instances solved as one unit, the CUDA-graph
+capture of chained stages, and parity of individual instances against the oracle (FLGF-AMR Sec. 3.4,
+FIF-AMR Sec. 3.5)."""
+import numpy as np
+import pytest
+
+import lgf_synth as S
+from oracle import amr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALPHA = 0.1
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2010_13213_gb300.lgf as L
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def table8(L):
+    t = L.lgf_table_create(8, (14, 14, 8), L.LGF_TBL_FP64 | L.LGF_TBL_DF32)
+    yield t
+    L.lgf_table_destroy(t)
+
+
+def small_instances(n=8):
+    out = []
+    for p in S.batch_instances(n, B=8):
+        q = dict(p)
+        q["nxy"] = min(p["nxy"], 48)
+        q["nz"] = max(32, 16 * int(np.ceil(q["nxy"] / 32)))
+        q["h_fine"] = (2 * p["R"] + 8 * p["sigma"]) / q["nxy"]
+        mesh, f, roles = S.ring_instance(q, B=8, n_ext=6)
+        out.append((mesh, np.concatenate(f, axis=1), roles))
+    return out
+
+
+@pytest.fixture(scope="module")
+def inst():
+    return small_instances()
+
+
+def make_batch(L, table, inst, precision=2):
+    meshes = [L.Mesh(m["levels"], m["B"], m["h0"], n_ext=m["n_ext"]) for m, _, _ in inst]
+    opts = L.make_opts(precision=precision)
+    return L.Batch(table, meshes, 3, L.LGF_F64, alpha=[ALPHA] * len(inst), opts=opts, nstreams=4), meshes
+
+
+def test_batch_stage_equals_individual_solves(L, table8, inst):
+    b, meshes = make_batch(L, table8, inst)
+    fs = [torch.from_numpy(f).cuda() for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    gs = [torch.zeros_like(f) for f in fs]
+    s = torch.cuda.Stream()
+    b.stage([f.data_ptr() for f in fs], [p.data_ptr() for p in phis], [g.data_ptr() for g in gs], s.cuda_stream)
+    torch.cuda.synchronize()
+    for i, (m, f) in enumerate(zip(meshes, fs)):
+        phi = torch.zeros_like(f)
+        g = torch.zeros_like(f)
+        L.lgf_poisson_solve(table8, m, 3, f.data_ptr(), phi.data_ptr(), L.LGF_F64, L.make_opts(precision=2))
+        L.lgf_heat_apply(table8, m, 3, f.data_ptr(), g.data_ptr(), L.LGF_F64, ALPHA, L.make_opts(precision=2))
+        torch.cuda.synchronize()
+        assert torch.equal(phi, phis[i]) and torch.equal(g, gs[i]), f"instance {i}"
+    b.close()
+
+
+def test_batch_instances_match_oracle(L, table8, inst):
+    b, meshes = make_batch(L, table8, inst)
+    fs = [torch.from_numpy(f).cuda() for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    gs = [torch.zeros_like(f) for f in fs]
+    b.stage([f.data_ptr() for f in fs], [p.data_ptr() for p in phis], [g.data_ptr() for g in gs])
+    torch.cuda.synchronize()
+    checked = set()
+    for i, (mesh, f, roles) in enumerate(inst):
+        K = len(mesh["levels"])
+        if K in checked or roles is not None:
+            continue
+        checked.add(K)
+        fl, o = [], 0
+        for blk in mesh["levels"]:
+            fl.append(f[:, o:o + len(blk)])
+            o += len(blk)
+        ref, masks = amr.flgf_amr(mesh, fl)
+        gref = amr.fif_amr(mesh, fl, ALPHA)
+        got = phis[i].cpu().numpy()
+        gg = gs[i].cpu().numpy()
+        o = 0
+        for k, blk in enumerate(mesh["levels"]):
+            msk = masks[k]
+            for c in range(2):
+                r = ref[k][c][msk]
+                assert np.abs(got[c, o:o + len(blk)][msk] - r).max() <= 1e-10 * np.abs(r).max()
+                gr = gref[k][c][msk]
+                assert np.abs(gg[c, o:o + len(blk)][msk] - gr).max() <= 1e-12 * np.abs(gr).max()
+            o += len(blk)
+    assert checked, "no multi-level instance in the batch"
+    b.close()
+
+
+def test_batch_graph_replays_chained_stages(L, table8, inst):
+    b, meshes = make_batch(L, table8, inst)
+    fs = [torch.from_numpy(f).cuda() for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    gs = [torch.zeros_like(f) for f in fs]
+    tmps = [torch.zeros_like(f) for f in fs]
+    s = torch.cuda.Stream()
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    b.graph_create(3, ptr(fs), ptr(phis), ptr(gs), ptr(tmps), s.cuda_stream)
+    assert b.graph_nodes() > 3 * len(inst)
+    for t in phis + gs + tmps:
+        t.zero_()
+    torch.cuda.synchronize()
+    b.graph_launch(s.cuda_stream)
+    torch.cuda.synchronize()
+    # eager chain: f -> (phi, g); g -> (phi, tmp); tmp -> (phi, g)
+    for i, (m, f) in enumerate(zip(meshes, fs)):
+        g1, g2, phi = torch.zeros_like(f), torch.zeros_like(f), torch.zeros_like(f)
+        src = f
+        for dst in (g1, g2, g1):
+            L.lgf_poisson_solve(table8, m, 3, src.data_ptr(), phi.data_ptr(), L.LGF_F64, L.make_opts(precision=2))
+            L.lgf_heat_apply(table8, m, 3, src.data_ptr(), dst.data_ptr(), L.LGF_F64, ALPHA, L.make_opts(precision=2))
+            src = dst
+        torch.cuda.synchronize()
+        assert torch.equal(phi, phis[i]), f"phi instance {i}"
+        assert torch.equal(g1, gs[i]), f"g instance {i}"
+    b.close()
+
+
+def test_batch_rejects_mismatched_block_size(L, table8):
+    m16 = L.Mesh([S.box_blocks((32, 32, 32), 16)], 16, 1.0)
+    with pytest.raises(L.LgfError) as e:
+        L.Batch(table8, [m16], 1)
+    assert e.value.status == L.LGF_E_MESH
