@@ -72,6 +72,8 @@ extern "C" {
 #define LGF_TBL_FP64 1u
 #define LGF_TBL_FP32 2u
 #define LGF_TBL_DF32 4u
+#define LGF_TBL_BOX_ONLY 8u  /* keep no per-offset spectra: only the block-index FFT mode is available
+                                 (its spectra are built per box shape on first use) */
 
 typedef struct lgf_table lgf_table; /* opaque: device LGF values + kernel spectra + workspaces */
 

@@ -194,13 +194,44 @@ def three_level_ring(R=1.0, sigma=0.2, B=16, thresholds=(1e-3, 1e-2), n_ext=16, 
     return mesh, f
 
 
+def _ring_s2_blockmin(nxyz, h, origin, B, R):
+    """Per block of a level grid: min over its cell centres of s^2 = z^2 + (r - R)^2 (ring about z)."""
+    nx, ny, nz = nxyz
+    x = _centres(nx, h, origin[0])
+    y = _centres(ny, h, origin[1])
+    z = _centres(nz, h, origin[2])
+    r = np.sqrt(x[None, :] ** 2 + y[:, None] ** 2)                      # [ny][nx]
+    d2 = ((r - R) ** 2).reshape(ny // B, B, nx // B, B).min(axis=(1, 3))  # [by][bx]
+    z2 = (z ** 2).reshape(nz // B, B).min(axis=1)                        # [bz]
+    return z2[:, None, None] + d2[None, :, :]                            # [bz][by][bx]
+
+
+def _ring_on_blocks(blocks, B, h, origin, R, sigma, gamma=1.0):
+    """Gaussian-core ring vorticity sampled at the cells of the given blocks: [3][nblk][B][B][B]."""
+    blocks = np.asarray(blocks)
+    loc = (np.arange(B) + 0.5) * h
+    out = np.zeros((3, len(blocks), B, B, B))
+    for i, (bx, by, bz) in enumerate(blocks):
+        x = origin[0] + bx * B * h + loc
+        y = origin[1] + by * B * h + loc
+        z = origin[2] + bz * B * h + loc
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        r = np.sqrt(X * X + Y * Y)
+        wt = gamma / (math.pi * sigma * sigma) * np.exp(-(Z * Z + (r - R) ** 2) / (sigma * sigma))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            out[0, i] = np.where(r > 0, -wt * Y / r, 0.0)
+            out[1, i] = np.where(r > 0, wt * X / r, 0.0)
+    return out
+
+
 def ring_instance(p, B=16, n_ext=16, thresholds=(1e-3, 1e-2), drop=1e-6):
     """Composite mesh of one batch instance (dict from ``batch_instances``): K = p["levels"] levels,
     finest spacing p["h_fine"], finest box p["nxy"]^2 x p["nz"] cells centred on the ring.  Level 0 covers
-    the box at its own spacing (rounded up to blocks) dilated by one block; for K = 3 level 1 holds the
-    blocks with |omega| > thresholds[0] max plus the parents of level 2; the finest level (K >= 2) holds
-    the blocks with |omega| > thresholds[1] max; for K = 1 the single level is the box, with source
-    blocks those reaching drop * max.  Returns (mesh, f_levels, roles or None)."""
+    the box at its own spacing (rounded up to blocks) dilated by one block (K > 1); for K = 3 level 1
+    holds the blocks with a cell where |omega| > thresholds[0] max plus the parents of level 2; the
+    finest level (K >= 2) the blocks with |omega| > thresholds[1] max; for K = 1 the single level is the
+    box, with source blocks those reaching drop * max.  max|omega| is the analytic peak Gamma/(pi sigma^2),
+    so |omega| > rel max is the cell-centre test s^2 < -sigma^2 ln(rel).  Returns (mesh, f_levels, roles)."""
     K, R, sig = p["levels"], p["R"], p["sigma"]
     hf = p["h_fine"]
     hs = [hf * 2 ** (K - 1 - k) for k in range(K)]
@@ -208,32 +239,26 @@ def ring_instance(p, B=16, n_ext=16, thresholds=(1e-3, 1e-2), drop=1e-6):
     scale = 2 ** (K - 1)
     n0 = tuple(int(math.ceil(n / scale / B)) * B + (2 * B if K > 1 else 0) for n in fine_n)
     origin = (-n0[0] * hs[0] / 2, -n0[1] * hs[0] / 2, -n0[2] * hs[0] / 2)
-
-    def field(nx, ny, nz, h):
-        return ring_vorticity(nx, ny, nz, h, R, sig, origin=origin)
-
     n_lev = [tuple(n * 2 ** k for n in n0) for k in range(K)]
-    vmax = np.sqrt((field(*n_lev[K - 1], hs[K - 1]) ** 2).sum(0)).max()
+
+    def above(k, rel):
+        m = _ring_s2_blockmin(n_lev[k], hs[k], origin, B, R) < -sig * sig * math.log(rel)
+        bz, by, bx = np.nonzero(m)
+        return np.stack([bx, by, bz], 1).astype(np.int32)
+
     blocks = [box_blocks((n0[2], n0[1], n0[0]), B)]
     roles = None
     if K == 1:
-        box = field(*n0, hs[0])
-        src = {tuple(b) for b in blocks_with_support(box, B, drop)}
+        src = {tuple(b) for b in above(0, drop)}
         roles = np.array([2 + (1 if tuple(b) in src else 0) for b in blocks[0]], np.uint8)
     if K >= 2:
-        fine = _level_blocks_over(field_fn=lambda nx, ny, nz, h, o: field(nx, ny, nz, h), nxyz=n_lev[K - 1],
-                                  h=hs[K - 1], origin=origin, B=B, rel=thresholds[1], vmax=vmax)
-        levels_mid = []
+        fine = above(K - 1, thresholds[1])
+        mid = []
         if K == 3:
-            mid = _level_blocks_over(field_fn=lambda nx, ny, nz, h, o: field(nx, ny, nz, h), nxyz=n_lev[1], h=hs[1],
-                                     origin=origin, B=B, rel=thresholds[0], vmax=vmax)
             parents = np.unique((fine * B // 2) // B, axis=0)
-            levels_mid = [np.unique(np.concatenate([mid, parents]), axis=0).astype(np.int32)]
-        blocks += levels_mid + [fine]
-    f = []
-    for k in range(K):
-        nx, ny, nz = n_lev[k]
-        f.append(box_to_blocks(field(nx, ny, nz, hs[k]), blocks[k], B))
+            mid = [np.unique(np.concatenate([above(1, thresholds[0]), parents]), axis=0).astype(np.int32)]
+        blocks += mid + [fine]
+    f = [_ring_on_blocks(blocks[k], B, hs[k], origin, R, sig) for k in range(K)]
     mesh = dict(B=B, h0=hs[0], n_ext=n_ext, levels=[np.ascontiguousarray(b, dtype=np.int32) for b in blocks])
     return mesh, f, roles
 

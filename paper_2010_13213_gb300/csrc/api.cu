@@ -90,7 +90,7 @@ int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_off
   for (int a = 0; a < 3; ++a)
     if (max_block_offset[a] < 0 || max_block_offset[a] > 64)
       return set_error(LGF_E_INVALID_ARG, "max_block_offset[%d] = %d out of [0, 64]", a, max_block_offset[a]);
-  if ((flags & 7u) == 0) return set_error(LGF_E_INVALID_ARG, "no spectrum format requested");
+  if ((flags & 15u) == 0) return set_error(LGF_E_INVALID_ARG, "no spectrum format requested");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   lgf_table *t = new lgf_table();
   cudaGetDevice(&t->device);
@@ -107,6 +107,10 @@ int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_off
   }
   const size_t W = (size_t)(2 * block) * (2 * block) * (block + 1);
   const size_t n = W * t->noff;
+  if (flags & LGF_TBL_BOX_ONLY) {
+    *out = t;  // pair spectra skipped; box spectra are generated on demand from t->Gd
+    return LGF_OK;
+  }
   if ((flags & LGF_TBL_FP64) && cudaMalloc(&t->s64, n * 16) != cudaSuccess) rc = LGF_E_OOM;
   if (!rc && (flags & LGF_TBL_FP32) && cudaMalloc(&t->s32, n * 8) != cudaSuccess) rc = LGF_E_OOM;
   if (!rc && (flags & LGF_TBL_DF32) && cudaMalloc(&t->sdf, n * 16) != cudaSuccess) rc = LGF_E_OOM;

@@ -138,8 +138,7 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
   int rc = get_plan(m, nullptr, &P);
   if (rc) return rc;
   if ((rc = check_range(P, t))) return rc;
-  const void *Gh = spectra_for<R>(t);
-  if (!Gh) return set_error(LGF_E_INVALID_ARG, "table lacks the spectra of the requested precision");
+  const void *Gh = spectra_for<R>(t);  // null for a box-only table: every level then runs in box mode
   const int B = P->B, K = P->K;
   const int64_t B3 = (int64_t)B * B * B;
   const int W = (2 * B) * (2 * B) * (B + 1);
@@ -164,7 +163,7 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
   for (int k = 0; k < K; ++k) {
     const LevelPlan &L = P->L[k];
     if (!L.box_ok || L.Tall.empty()) continue;
-    if (o.mac_mode == LGF_MAC_BOX) {
+    if (o.mac_mode == LGF_MAC_BOX || !Gh) {
       use_box[k] = 1;
     } else if (o.mac_mode == LGF_MAC_AUTO) {
       const bool packAB = !L.Tpsi.empty() || !L.SB.empty();
@@ -175,10 +174,11 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     }
     if (use_box[k]) maxbox = std::max<int64_t>(maxbox, 8 * L.nbox * B3);
   }
-  if (o.mac_mode == LGF_MAC_BOX)
-    for (int k = 0; k < K; ++k)
-      if (!use_box[k] && !P->L[k].Tall.empty())
-        return set_error(LGF_E_UNSUPPORTED, "BOX mode needs 1..16 blocks per axis on level %d", k);
+  for (int k = 0; k < K; ++k)
+    if (!use_box[k] && !P->L[k].Tall.empty() && (o.mac_mode == LGF_MAC_BOX || !Gh))
+      return set_error(Gh ? LGF_E_UNSUPPORTED : LGF_E_INVALID_ARG,
+                       "level %d needs the pair mode (box over 16 blocks per axis) and the table has no %s", k,
+                       Gh ? "box support for it" : "pair spectra of this precision");
   Workspace *ws = workspace_for(t, st);
   const size_t field = sizeof(R) * (size_t)ncomp * maxBL * B3;
   const size_t ybytes = sizeof(cx<R>) * (size_t)maxbox;

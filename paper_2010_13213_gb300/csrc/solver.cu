@@ -252,8 +252,9 @@ static int solve_single_any(lgf_table *t, const lgf_mesh *m, int ncomp, const vo
   if (P->ntgt == 0) return LGF_OK;
   int mode = o.mac_mode;
   if (mode == LGF_MAC_AUTO)
-    mode = (P->box_ok && box_cost(m->block, P->nb) < pair_cost(m->block, P->nsrc, P->ntgt)) ? LGF_MAC_BOX
-                                                                                             : LGF_MAC_PAIR;
+    mode = (P->box_ok && (!spectra_of<R>(t) || box_cost(m->block, P->nb) < pair_cost(m->block, P->nsrc, P->ntgt)))
+               ? LGF_MAC_BOX
+               : LGF_MAC_PAIR;
   if (mode == LGF_MAC_BOX) {
     if (!P->box_ok) return set_error(LGF_E_UNSUPPORTED, "BOX mode needs 1..%d blocks per axis", BOX_NB_MAX);
     return solve_single_box<R>(t, m, P, ncomp, f, phi, dtype, o, rep, st);

@@ -28,7 +28,7 @@ LGF_E_UNSUPPORTED = -8
 LGF_F64, LGF_F32 = 0, 1
 LGF_PREC_FP64, LGF_PREC_FP32, LGF_PREC_DF32 = 0, 1, 2
 LGF_MAC_AUTO, LGF_MAC_PAIR, LGF_MAC_BOX = 0, 1, 2
-LGF_TBL_FP64, LGF_TBL_FP32, LGF_TBL_DF32 = 1, 2, 4
+LGF_TBL_FP64, LGF_TBL_FP32, LGF_TBL_DF32, LGF_TBL_BOX_ONLY = 1, 2, 4, 8
 PHASES = ("restrict", "correction", "forward", "mac", "inverse", "interp", "residual", "heat")
 
 
