@@ -57,14 +57,27 @@ struct OutSpec {
   int dtype, bits;
 };
 
+#define BOX_MAXF 4  // complex fields per launch
+
+struct InSpec3 {  // the input specs of one complex field
+  InSpec s[3];
+};
+
+struct FwdSpecs {   // per field: up to three input specs (first forward pass only)
+  InSpec s[BOX_MAXF][3];
+  int n[BOX_MAXF];
+};
+
 // ------------------------------------------------------------------ block-index DFT, forward
 // Pass along axis `ax`: for every line (the two other block coordinates within `ext`) and every
-// local cell m, out[.. k ..][m] = sum_{j < nb} W_P^{j k} in[.. j ..][m], k < P.  The first pass
-// (nspec > 0) gathers its input from the specs instead of `in`.
+// local cell m, out[.. k ..][m] = sum_{j < nb} W_P^{j k} in[.. j ..][m], k < P.  grid.z = 2 * field +
+// half: each CTA produces the even (half 0) or odd (half 1) outputs k of one field.  The first pass
+// (gather != 0) reads its input through the field's specs instead of `in`.  Field f's arrays start at
+// in + f * fstride, out + f * fstride.
 template <class R, int B>
 __global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
-                                                  BoxGeom g, int ax, int3 ext, BoxTw<R> tw, int nspec,
-                                                  InSpec s0, InSpec s1, InSpec s2) {
+                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
+                                                  int gather, FwdSpecs sp) {
   constexpr int B3 = B * B * B;
   const int nb = g.nb[ax];
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
@@ -72,14 +85,18 @@ __global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, 
   const int64_t line = blockIdx.y;
   const int l1 = (int)(line % e1), l2 = (int)(line / e1);
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int field = blockIdx.z >> 1, half = blockIdx.z & 1;
   if (m >= B3) return;
-  // addresses along the pass axis: box array element (base + j * bstride) * B3 + m, gather index gbase + j * gstride
+  in += field * fstride;
+  out += field * fstride;
+  // addresses along the pass axis: box array element (base + j * bsa) * B3 + m, gather index gbase + j * gsa
   const int64_t bsa = g.bs[ax];
   const int64_t base = (int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2];
   const int64_t gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1]);
   const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
   const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
   const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
+  const int ns = gather ? sp.n[field] : 0;
   auto add_spec = [&](const InSpec &s, int64_t bidx, R &re, R &im) {
     const int idx = s.gather[bidx];
     if (idx < 0) return;
@@ -90,41 +107,40 @@ __global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, 
     else re = re + v;
   };
   auto elem_in = [&](int j) -> cx<R> {
-    if (nspec) {
+    if (gather) {
       const int64_t bidx = gbase + j * gsa;
       R re = RT<R>::zero(), im = RT<R>::zero();
-      add_spec(s0, bidx, re, im);
-      if (nspec > 1) add_spec(s1, bidx, re, im);
-      if (nspec > 2) add_spec(s2, bidx, re, im);
+      if (ns > 0) add_spec(sp.s[field][0], bidx, re, im);
+      if (ns > 1) add_spec(sp.s[field][1], bidx, re, im);
+      if (ns > 2) add_spec(sp.s[field][2], bidx, re, im);
       return cx<R>{re, im};
     }
     return in[(base + j * bsa) * B3 + m];
   };
   const int P = 2 * nb;
-  for (int half = 0; half < 2; ++half) {
-    cx<R> acc[BOX_NB_MAX];
+  cx<R> acc[BOX_NB_MAX];
 #pragma unroll
-    for (int k = 0; k < BOX_NB_MAX; ++k) acc[k] = cx_zero<R>();
-    for (int j = 0; j < nb; ++j) {
-      const cx<R> x = elem_in(j);
-      int n = half ? j : 0;  // (j * (2k + half)) mod P for k = 0, 1, ...
-      const int step = (2 * j) % P;
+  for (int k = 0; k < BOX_NB_MAX; ++k) acc[k] = cx_zero<R>();
+  for (int j = 0; j < nb; ++j) {
+    const cx<R> x = elem_in(j);
+    int n = half ? j : 0;  // (j * (2k + half)) mod P for k = 0, 1, ...
+    const int step = (2 * j) % P;
 #pragma unroll
-      for (int k = 0; k < BOX_NB_MAX; ++k) {
-        if (k < nb) acc[k] = n ? cmac(acc[k], x, tw.w[n]) : cnorm(cadd(acc[k], x));
-        n += step;
-        if (n >= P) n -= P;
-      }
+    for (int k = 0; k < BOX_NB_MAX; ++k) {
+      if (k < nb) acc[k] = n ? cmac_lazy(acc[k], x, tw.w[n]) : cadd(acc[k], x);
+      n += step;
+      if (n >= P) n -= P;
     }
-#pragma unroll
-    for (int k = 0; k < BOX_NB_MAX; ++k)
-      if (k < nb) out[(base + (int64_t)(2 * k + half) * bsa) * B3 + m] = acc[k];
   }
+#pragma unroll
+  for (int k = 0; k < BOX_NB_MAX; ++k)
+    if (k < nb) out[(base + (int64_t)(2 * k + half) * bsa) * B3 + m] = cnorm(acc[k]);
 }
 
 // ------------------------------------------------------------------ block-index DFT, inverse
-// out[.. j ..][m] = sum_{k < P} W_P^{-j k} in[.. k ..][m] for j < nb (unnormalised).  The last pass
-// (final != 0) writes scale * re and scale * im through the two output specs instead of `out`.
+// out[.. j ..][m] = sum_{k < P} W_P^{-j k} in[.. k ..][m] for j < nb (unnormalised).  grid.z =
+// 2 * field + part: part 0 computes outputs j < ceil(nb/2), part 1 the rest.  The last pass
+// (final != 0) writes scale * re and scale * im through the field's output specs instead of `out`.
 template <class R>
 LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
   if (!o.scatter) return;
@@ -136,10 +152,15 @@ LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
   store_field<R>(o.dst, o.off + (int64_t)ob * B3 + m, o.dtype, v);
 }
 
+template <class R>
+struct InvOuts {  // per field: destinations of the real and imaginary parts (last inverse pass)
+  OutSpec<R> re[BOX_MAXF], im[BOX_MAXF];
+};
+
 template <class R, int B>
 __global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
-                                                  BoxGeom g, int ax, int3 ext, BoxTw<R> tw, int final,
-                                                  OutSpec<R> ore, OutSpec<R> oim, double scale) {
+                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
+                                                  int final, InvOuts<R> outs, double scale) {
   constexpr int B3 = B * B * B;
   const int nb = g.nb[ax];
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
@@ -147,27 +168,32 @@ __global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, 
   const int64_t line = blockIdx.y;
   const int l1 = (int)(line % e1), l2 = (int)(line / e1);
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int field = blockIdx.z >> 1, part = blockIdx.z & 1;
   if (m >= B3) return;
+  in += field * fstride;
+  out += field * fstride;
+  const int nh = (nb + 1) >> 1;
+  const int j0 = part ? nh : 0, nj = part ? nb - nh : nh;
   const int64_t bsa = g.bs[ax];
   const int64_t base = (int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2];
   const int P = 2 * nb;
-  cx<R> acc[BOX_NB_MAX];
+  cx<R> acc[(BOX_NB_MAX + 1) / 2];
 #pragma unroll
-  for (int j = 0; j < BOX_NB_MAX; ++j) acc[j] = cx_zero<R>();
+  for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j) acc[j] = cx_zero<R>();
   for (int k = 0; k < P; ++k) {
     const cx<R> x = in[(base + k * bsa) * B3 + m];
-    int n = 0;  // (j * k) mod P for j = 0, 1, ...
+    int n = (j0 * k) % P;  // (j * k) mod P for j = j0, j0 + 1, ...
 #pragma unroll
-    for (int j = 0; j < BOX_NB_MAX; ++j) {
-      if (j < nb) acc[j] = n ? cmac(acc[j], x, conj(tw.w[n])) : cnorm(cadd(acc[j], x));
+    for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j) {
+      if (j < nj) acc[j] = n ? cmac_lazy(acc[j], x, conj(tw.w[n])) : cadd(acc[j], x);
       n += k;
       if (n >= P) n -= P;
     }
   }
   if (!final) {
 #pragma unroll
-    for (int j = 0; j < BOX_NB_MAX; ++j)
-      if (j < nb) out[(base + (int64_t)j * bsa) * B3 + m] = acc[j];
+    for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j)
+      if (j < nj) out[(base + (int64_t)(j0 + j) * bsa) * B3 + m] = cnorm(acc[j]);
     return;
   }
   const R sc = RT<R>::from(scale);
@@ -176,11 +202,12 @@ __global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, 
   const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
   const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
 #pragma unroll
-  for (int j = 0; j < BOX_NB_MAX; ++j) {
-    if (j >= nb) continue;
-    const int bidx = (int)(gbase + j * gsa);
-    box_store<R>(ore, bidx, m, B3, acc[j].re * sc);
-    box_store<R>(oim, bidx, m, B3, acc[j].im * sc);
+  for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j) {
+    if (j >= nj) continue;
+    const int bidx = (int)(gbase + (j0 + j) * gsa);
+    const cx<R> v = cnorm(acc[j]);
+    box_store<R>(outs.re[field], bidx, m, B3, v.re * sc);
+    box_store<R>(outs.im[field], bidx, m, B3, v.im * sc);
   }
 }
 
@@ -234,9 +261,11 @@ struct MidGeom {
 };
 
 template <class R, int B, bool MULTIPLY>
-__global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, const R *__restrict__ Gh, BoxGeom g,
-                                                 const cx<R> *__restrict__ twx, const cx<R> *__restrict__ twy,
-                                                 const cx<R> *__restrict__ twz, Tw64<R> tw, R *__restrict__ kout) {
+__global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64_t fstride,
+                                                    const R *__restrict__ Gh, BoxGeom g,
+                                                    const cx<R> *__restrict__ twx, const cx<R> *__restrict__ twy,
+                                                    const cx<R> *__restrict__ twz, Tw64<R> tw,
+                                                    R *__restrict__ kout) {
   constexpr int B3 = B * B * B, RS = B + 1;
   extern __shared__ unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
@@ -251,7 +280,7 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, const
     const cx<R> *tab = a == 0 ? twx : (a == 1 ? twy : twz);
     T[a][mm] = tab[(int)(((int64_t)mm * k1) % Pc)];
   }
-  cx<R> *Yb = Y + kb * B3;
+  cx<R> *Yb = Y + blockIdx.y * fstride + kb * B3;  // field blockIdx.y
   for (int i = threadIdx.x; i < B3; i += blockDim.x) {
     const int x = i % B, y = (i / B) % B, z = i / (B * B);
     S[(z * B + y) * RS + x] = Yb[i];

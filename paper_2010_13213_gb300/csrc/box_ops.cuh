@@ -43,17 +43,18 @@ inline BoxTw<R> btw_of(const BoxSpec *S, int a) {
 
 template <class R>
 struct BoxOps {
-  // Convolution of one complex field on the box: forward (gathering from the specs), kernel,
-  // inverse (scattering through the output specs).  Y0/Y1: P^3 B^3 complex R each.
-  // `mark(phase)` is called after the forward, kernel and inverse stages (phase timing; may be null).
-  static int convolve(int B, const BoxSpec *S, int nspec, const InSpec *in, const OutSpec<R> &ore,
-                      const OutSpec<R> &oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
-                      void (*mark)(void *, int) = nullptr, void *mark_ctx = nullptr);
+  // Convolutions of `nf` complex fields on the box: forward (gathering through in[f][0..nin[f])),
+  // kernel, inverse (scattering through ore[f] / oim[f]).  Y0/Y1 hold min(nf, BOX_MAXF) * P^3 B^3
+  // complex R each.  `mark(phase)` is called after the forward, kernel and inverse stages of every
+  // group of fields (phase timing; may be null).
+  static int convolve(int B, const BoxSpec *S, int nf, const int *nin, const InSpec3 *in,
+                      const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1,
+                      cudaStream_t st, void (*mark)(void *, int) = nullptr, void *mark_ctx = nullptr);
 };
 
 template <class R, int B>
-static int box_convolve_b(const BoxSpec *S, int nspec, const InSpec *in, const OutSpec<R> &ore,
-                          const OutSpec<R> &oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
+static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec3 *in, const OutSpec<R> *ore,
+                          const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
                           void (*mark)(void *, int), void *mark_ctx) {
   constexpr int B3 = B * B * B;
   BoxGeom g;
@@ -64,48 +65,58 @@ static int box_convolve_b(const BoxSpec *S, int nspec, const InSpec *in, const O
   g.bs[0] = 1;
   g.bs[1] = g.P[0];
   g.bs[2] = (int64_t)g.P[0] * g.P[1];
-  const unsigned gx = (B3 + 255) / 256;
-  InSpec sp[3] = {};
-  for (int i = 0; i < nspec && i < 3; ++i) sp[i] = in[i];
   const int *nb = g.nb, *P = g.P;
-  // forward x (gather), y, z
-  k_bdft_fwd<R, B><<<dim3(gx, nb[1] * nb[2]), 256, 0, st>>>(nullptr, Y0, g, 0, make_int3(0, nb[1], nb[2]),
-                                                            btw_of<R>(S, 0), nspec, sp[0], sp[1], sp[2]);
-  k_bdft_fwd<R, B><<<dim3(gx, P[0] * nb[2]), 256, 0, st>>>(Y0, Y1, g, 1, make_int3(P[0], 0, nb[2]),
-                                                           btw_of<R>(S, 1), 0, sp[0], sp[1], sp[2]);
-  k_bdft_fwd<R, B><<<dim3(gx, P[0] * P[1]), 256, 0, st>>>(Y1, Y0, g, 2, make_int3(P[0], P[1], 0),
-                                                          btw_of<R>(S, 2), 0, sp[0], sp[1], sp[2]);
-  if (mark) mark(mark_ctx, 2);
-  // fused twiddle / local FFT / kernel / inverse
+  const int64_t nblk = (int64_t)P[0] * P[1] * P[2];
+  const int64_t fstride = nblk * B3;
+  const unsigned gx = (B3 + 255) / 256;
   const size_t sm = sizeof(cx<R>) * (size_t)B * B * (B + 1);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_box_mid<R, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  const int64_t nblk = (int64_t)P[0] * P[1] * P[2];
-  k_box_mid<R, B, true><<<(unsigned)nblk, 256, sm, st>>>(Y0, spec_of<R>(S), g, tw_of<R>(S, 0), tw_of<R>(S, 1),
-                                                         tw_of<R>(S, 2), make_tw64<R>(), nullptr);
-  if (mark) mark(mark_ctx, 3);
-  // inverse z, y, x (scatter)
-  OutSpec<R> none{};
-  k_bdft_inv<R, B><<<dim3(gx, P[0] * P[1]), 256, 0, st>>>(Y0, Y1, g, 2, make_int3(P[0], P[1], 0), btw_of<R>(S, 2),
-                                                          0, none, none, 1.0);
-  k_bdft_inv<R, B><<<dim3(gx, P[0] * nb[2]), 256, 0, st>>>(Y1, Y0, g, 1, make_int3(P[0], 0, nb[2]),
-                                                           btw_of<R>(S, 1), 0, none, none, 1.0);
-  k_bdft_inv<R, B><<<dim3(gx, nb[1] * nb[2]), 256, 0, st>>>(Y0, Y1, g, 0, make_int3(0, nb[1], nb[2]),
-                                                            btw_of<R>(S, 0), 1, ore, oim, scale);
-  if (mark) mark(mark_ctx, 4);
+  for (int f0 = 0; f0 < nf; f0 += BOX_MAXF) {
+    const int n = nf - f0 < BOX_MAXF ? nf - f0 : BOX_MAXF;
+    FwdSpecs sp{};
+    InvOuts<R> outs{};
+    for (int f = 0; f < n; ++f) {
+      sp.n[f] = nin[f0 + f];
+      for (int i = 0; i < sp.n[f] && i < 3; ++i) sp.s[f][i] = in[f0 + f].s[i];
+      outs.re[f] = ore[f0 + f];
+      outs.im[f] = oim[f0 + f];
+    }
+    const unsigned zf = 2 * n;
+    // forward x (gather), y, z
+    k_bdft_fwd<R, B><<<dim3(gx, nb[1] * nb[2], zf), 256, 0, st>>>(nullptr, Y0, fstride, g, 0,
+                                                                  make_int3(0, nb[1], nb[2]), btw_of<R>(S, 0), 1, sp);
+    k_bdft_fwd<R, B><<<dim3(gx, P[0] * nb[2], zf), 256, 0, st>>>(Y0, Y1, fstride, g, 1, make_int3(P[0], 0, nb[2]),
+                                                                 btw_of<R>(S, 1), 0, sp);
+    k_bdft_fwd<R, B><<<dim3(gx, P[0] * P[1], zf), 256, 0, st>>>(Y1, Y0, fstride, g, 2, make_int3(P[0], P[1], 0),
+                                                                btw_of<R>(S, 2), 0, sp);
+    if (mark) mark(mark_ctx, 2);
+    k_box_mid<R, B, true><<<dim3((unsigned)nblk, n), 256, sm, st>>>(Y0, fstride, spec_of<R>(S), g, tw_of<R>(S, 0),
+                                                                   tw_of<R>(S, 1), tw_of<R>(S, 2), make_tw64<R>(),
+                                                                   nullptr);
+    if (mark) mark(mark_ctx, 3);
+    k_bdft_inv<R, B><<<dim3(gx, P[0] * P[1], zf), 256, 0, st>>>(Y0, Y1, fstride, g, 2, make_int3(P[0], P[1], 0),
+                                                                btw_of<R>(S, 2), 0, outs, 1.0);
+    k_bdft_inv<R, B><<<dim3(gx, P[0] * nb[2], zf), 256, 0, st>>>(Y1, Y0, fstride, g, 1, make_int3(P[0], 0, nb[2]),
+                                                                 btw_of<R>(S, 1), 0, outs, 1.0);
+    k_bdft_inv<R, B><<<dim3(gx, nb[1] * nb[2], zf), 256, 0, st>>>(Y0, Y1, fstride, g, 0,
+                                                                  make_int3(0, nb[1], nb[2]), btw_of<R>(S, 0), 1,
+                                                                  outs, scale);
+    if (mark) mark(mark_ctx, 4);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "box convolution launch: %s", cudaGetErrorString(e));
 }
 
 template <class R>
-int BoxOps<R>::convolve(int B, const BoxSpec *S, int nspec, const InSpec *in, const OutSpec<R> &ore,
-                        const OutSpec<R> &oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
-                        void (*mark)(void *, int), void *mark_ctx) {
-  if (B == 8) return box_convolve_b<R, 8>(S, nspec, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
-  if (B == 16) return box_convolve_b<R, 16>(S, nspec, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
+int BoxOps<R>::convolve(int B, const BoxSpec *S, int nf, const int *nin, const InSpec3 *in,
+                        const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1,
+                        cudaStream_t st, void (*mark)(void *, int), void *mark_ctx) {
+  if (B == 8) return box_convolve_b<R, 8>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
+  if (B == 16) return box_convolve_b<R, 16>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
   return set_error(LGF_E_UNSUPPORTED, "block size %d", B);
 }
 

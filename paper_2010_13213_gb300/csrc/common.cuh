@@ -175,6 +175,24 @@ LGF_D df df_dot2_acc(df acc, df a, df b, df c, df d, float sgn) {
   const float lo = __fadd_rn(__fadd_rn(acc.lo, x), __fadd_rn(t1, t2));
   return df_renorm(df{s2, lo});
 }
+// acc + a*b + sgn * c*d without the final renormalisation (accumulators of a few terms)
+LGF_D df df_dot2_acc_lazy(df acc, df a, df b, df c, df d, float sgn) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  const float p2 = __fmul_rn(sgn * c.hi, d.hi);
+  const float e2 = __fmaf_rn(sgn * c.hi, d.hi, -p2);
+  float x = __fmaf_rn(a.lo, b.hi, e1);
+  x = __fmaf_rn(a.hi, b.lo, x);
+  x = __fmaf_rn(sgn * c.lo, d.hi, x);
+  x = __fmaf_rn(sgn * c.hi, d.lo, __fadd_rn(x, e2));
+  float s = __fadd_rn(acc.hi, p1);
+  float bb = __fsub_rn(s, acc.hi);
+  const float t1 = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p1, bb));
+  const float s2 = __fadd_rn(s, p2);
+  bb = __fsub_rn(s2, s);
+  const float t2 = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(p2, bb));
+  return df{s2, __fadd_rn(__fadd_rn(acc.lo, x), __fadd_rn(t1, t2))};
+}
 template <>
 LGF_D cx<df> cadd<df>(cx<df> a, cx<df> b) { return {df_add_lazy(a.re, b.re), df_add_lazy(a.im, b.im)}; }
 template <>
@@ -187,6 +205,13 @@ template <>
 LGF_D cx<df> cnorm<df>(cx<df> a) { return {df_renorm(a.re), df_renorm(a.im)}; }
 LGF_D cx<df> cmac(cx<df> acc, cx<df> a, cx<df> b) {
   return {df_dot2_acc(acc.re, a.re, b.re, a.im, b.im, -1.0f), df_dot2_acc(acc.im, a.re, b.im, a.im, b.re, 1.0f)};
+}
+// multiply-add leaving a double-float accumulator unnormalised (callers apply cnorm at the end)
+LGF_D cx<double> cmac_lazy(cx<double> acc, cx<double> a, cx<double> b) { return cmac(acc, a, b); }
+LGF_D cx<float> cmac_lazy(cx<float> acc, cx<float> a, cx<float> b) { return cmac(acc, a, b); }
+LGF_D cx<df> cmac_lazy(cx<df> acc, cx<df> a, cx<df> b) {
+  return {df_dot2_acc_lazy(acc.re, a.re, b.re, a.im, b.im, -1.0f),
+          df_dot2_acc_lazy(acc.im, a.re, b.im, a.im, b.re, 1.0f)};
 }
 
 // Twiddles W_64^j = cos(2 pi j / 64) - i sin(2 pi j / 64), j < 64, passed by value as a kernel

@@ -172,7 +172,7 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
                         pair_cost(B, (double)L.SB.size(), (double)L.Tphi.size());
       use_box[k] = cb < cp;
     }
-    if (use_box[k]) maxbox = std::max<int64_t>(maxbox, 8 * L.nbox * B3);
+    if (use_box[k]) maxbox = std::max<int64_t>(maxbox, (int64_t)std::min(ncomp, BOX_MAXF) * 8 * L.nbox * B3);
   }
   for (int k = 0; k < K; ++k)
     if (!use_box[k] && !P->L[k].Tall.empty() && (o.mac_mode == LGF_MAC_BOX || !Gh))
@@ -242,46 +242,50 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       const bool packAB = nPsi > 0 || nSB > 0;
       const R *cadd = k > 0 ? c : nullptr;
       cx<R> *Y0 = (cx<R> *)ws->buf[0].p, *Y1 = (cx<R> *)ws->buf[1].p;
+      std::vector<int> nin;
+      std::vector<InSpec3> in;
+      std::vector<OutSpec<R>> ore, oim;
       if (packAB) {
         // z = A + i (A + B): real part -> psi_k on the psi targets, imaginary part -> phi on Omega_k
         for (int cc = 0; cc < ncomp; ++cc) {
-          InSpec in[3];
+          InSpec sp[3];
           int ns = 0;
           if (nSA) {
-            in[ns++] = InSpec{gA, A + cc * cs[k], nullptr, 2, 0, 0};
-            in[ns++] = InSpec{gA, A + cc * cs[k], nullptr, 2, 0, 1};
+            sp[ns++] = InSpec{gA, A + cc * cs[k], nullptr, 2, 0, 0};
+            sp[ns++] = InSpec{gA, A + cc * cs[k], nullptr, 2, 0, 1};
           }
-          if (nSB) in[ns++] = InSpec{gB, Fall + Foff[k] + cc * cs[k], L.d_cellmask, 2, CB_COV, 1};
-          OutSpec<R> ore{nPsi ? sPsi : nullptr, nullptr, Psi + Foff[k], cadd ? cadd + cc * cs[k] : nullptr, nullptr,
-                         cc * cs[k], 2, 0};
-          OutSpec<R> oim{nPhi ? sPhi : nullptr, nullptr, phi, cadd ? cadd + cc * cs[k] : nullptr, L.d_cellmask,
-                         cc * ucs + L.user_off * B3, dtype, CB_OM};
-          if (ns == 0) continue;
-          if ((rc = BoxOps<R>::convolve(B, S, ns, in, ore, oim, scale, Y0, Y1, st, o.timing ? phase_mark_cb : nullptr,
-                                        &tm)))
-            return rc;
-          launches += 7;
+          if (nSB) sp[ns++] = InSpec{gB, Fall + Foff[k] + cc * cs[k], L.d_cellmask, 2, CB_COV, 1};
+          nin.push_back(ns);
+          in.emplace_back();
+          for (int q = 0; q < 3; ++q) in.back().s[q] = sp[q];
+          ore.push_back(OutSpec<R>{nPsi ? sPsi : nullptr, nullptr, Psi + Foff[k], cadd ? cadd + cc * cs[k] : nullptr,
+                                   nullptr, cc * cs[k], 2, 0});
+          oim.push_back(OutSpec<R>{nPhi ? sPhi : nullptr, nullptr, phi, cadd ? cadd + cc * cs[k] : nullptr,
+                                   L.d_cellmask, cc * ucs + L.user_off * B3, dtype, CB_OM});
         }
       } else {
         // finest level without psi targets: two components per complex field, both to phi
         for (int c0 = 0; c0 < ncomp; c0 += 2) {
           const int c1 = c0 + 1;
-          InSpec in[2];
+          InSpec sp[3] = {};
           int ns = 0;
-          in[ns++] = InSpec{gA, A + c0 * cs[k], nullptr, 2, 0, 0};
-          if (c1 < ncomp) in[ns++] = InSpec{gA, A + c1 * cs[k], nullptr, 2, 0, 1};
-          OutSpec<R> ore{sPhi, nullptr, phi, cadd ? cadd + c0 * cs[k] : nullptr, L.d_cellmask,
-                         c0 * ucs + L.user_off * B3, dtype, CB_OM};
-          OutSpec<R> oim{};
-          if (c1 < ncomp)
-            oim = OutSpec<R>{sPhi, nullptr, phi, cadd ? cadd + c1 * cs[k] : nullptr, L.d_cellmask,
-                             c1 * ucs + L.user_off * B3, dtype, CB_OM};
-          if ((rc = BoxOps<R>::convolve(B, S, ns, in, ore, oim, scale, Y0, Y1, st, o.timing ? phase_mark_cb : nullptr,
-                                        &tm)))
-            return rc;
-          launches += 7;
+          sp[ns++] = InSpec{gA, A + c0 * cs[k], nullptr, 2, 0, 0};
+          if (c1 < ncomp) sp[ns++] = InSpec{gA, A + c1 * cs[k], nullptr, 2, 0, 1};
+          nin.push_back(ns);
+          in.emplace_back();
+          for (int q = 0; q < 3; ++q) in.back().s[q] = sp[q];
+          ore.push_back(OutSpec<R>{sPhi, nullptr, phi, cadd ? cadd + c0 * cs[k] : nullptr, L.d_cellmask,
+                                   c0 * ucs + L.user_off * B3, dtype, CB_OM});
+          oim.push_back(c1 < ncomp ? OutSpec<R>{sPhi, nullptr, phi, cadd ? cadd + c1 * cs[k] : nullptr, L.d_cellmask,
+                                                c1 * ucs + L.user_off * B3, dtype, CB_OM}
+                                   : OutSpec<R>{});
         }
       }
+      const int nf = (int)nin.size();
+      if ((rc = BoxOps<R>::convolve(B, S, nf, nin.data(), in.data(), ore.data(), oim.data(), scale, Y0, Y1, st,
+                                    o.timing ? phase_mark_cb : nullptr, &tm)))
+        return rc;
+      launches += 7 * ((nf + BOX_MAXF - 1) / BOX_MAXF);
       target_cells += L.n_omega;
       nsrc_total += nSA + nSB;
       ntgt_total += nT;

@@ -211,7 +211,8 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
   int rc = box_spectrum(t, P->nb, &S, st);
   if (rc) return rc;
   Workspace *ws = workspace_for(t, st);
-  const size_t ybytes = sizeof(cx<R>) * (size_t)(8 * P->nbox) * B3;
+  const int nf = (ncomp + 1) / 2;
+  const size_t ybytes = sizeof(cx<R>) * (size_t)std::min(nf, BOX_MAXF) * (8 * P->nbox) * B3;
   if ((rc = ws->buf[0].reserve(ybytes)) || (rc = ws->buf[1].reserve(ybytes))) return rc;
   const int32_t *gmap = P->d_idx + P->nsrc + P->ntgt, *smap = gmap + P->nbox;
   PhaseTimer tm;
@@ -219,21 +220,23 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
   const int64_t cs = (int64_t)n * B3;
   const size_t es = dtype_size(dtype, sizeof(R));
   const double scale = m->h0 * m->h0 / (8.0 * P->nbox * (double)B3);
-  int64_t launches = 0;
-  for (int c0 = 0; c0 < ncomp; c0 += 2) {
-    const int c1 = c0 + 1;
-    InSpec in[2];
-    in[0] = InSpec{gmap, (const char *)f + es * c0 * cs, nullptr, dtype, 0, 0};
-    int nspec = 1;
-    if (c1 < ncomp) in[nspec++] = InSpec{gmap, (const char *)f + es * c1 * cs, nullptr, dtype, 0, 1};
-    OutSpec<R> ore{smap, nullptr, phi, nullptr, nullptr, c0 * cs, dtype, 0};
-    OutSpec<R> oim{};
-    if (c1 < ncomp) oim = OutSpec<R>{smap, nullptr, phi, nullptr, nullptr, c1 * cs, dtype, 0};
-    if ((rc = BoxOps<R>::convolve(B, S, nspec, in, ore, oim, scale, (cx<R> *)ws->buf[0].p, (cx<R> *)ws->buf[1].p,
-                                  st, o.timing ? phase_mark_cb : nullptr, &tm)))
-      return rc;
-    launches += 7;
+  // two components per complex field
+  std::vector<int> nin(nf);
+  std::vector<InSpec3> in(nf);
+  std::vector<OutSpec<R>> ore(nf), oim(nf);
+  for (int fi = 0; fi < nf; ++fi) {
+    const int c0 = 2 * fi, c1 = c0 + 1;
+    nin[fi] = 1;
+    in[fi].s[0] = InSpec{gmap, (const char *)f + es * c0 * cs, nullptr, dtype, 0, 0};
+    if (c1 < ncomp) in[fi].s[nin[fi]++] = InSpec{gmap, (const char *)f + es * c1 * cs, nullptr, dtype, 0, 1};
+    ore[fi] = OutSpec<R>{smap, nullptr, phi, nullptr, nullptr, c0 * cs, dtype, 0};
+    oim[fi] = c1 < ncomp ? OutSpec<R>{smap, nullptr, phi, nullptr, nullptr, c1 * cs, dtype, 0} : OutSpec<R>{};
   }
+  if ((rc = BoxOps<R>::convolve(B, S, nf, nin.data(), in.data(), ore.data(), oim.data(), scale,
+                                (cx<R> *)ws->buf[0].p, (cx<R> *)ws->buf[1].p, st,
+                                o.timing ? phase_mark_cb : nullptr, &tm)))
+    return rc;
+  const int64_t launches = 7 * ((nf + BOX_MAXF - 1) / BOX_MAXF);
   tm.finish(rep);
   fill_report(rep, P, B3, ws, launches, LGF_MAC_BOX, (int64_t)S->bytes);
   if (o.timing) {
