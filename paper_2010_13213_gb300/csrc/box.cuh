@@ -96,7 +96,20 @@ __global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, 
   const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
   const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
   const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
-  const int ns = gather ? sp.n[field] : 0;
+  // per-field specs copied with compile-time indices (a dynamic index would copy the parameter block
+  // to local memory)
+  InSpec s0{}, s1{}, s2{};
+  int ns = 0;
+  if (gather) {
+#pragma unroll
+    for (int f = 0; f < BOX_MAXF; ++f)
+      if (f == field) {
+        s0 = sp.s[f][0];
+        s1 = sp.s[f][1];
+        s2 = sp.s[f][2];
+        ns = sp.n[f];
+      }
+  }
   auto add_spec = [&](const InSpec &s, int64_t bidx, R &re, R &im) {
     const int idx = s.gather[bidx];
     if (idx < 0) return;
@@ -110,9 +123,9 @@ __global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, 
     if (gather) {
       const int64_t bidx = gbase + j * gsa;
       R re = RT<R>::zero(), im = RT<R>::zero();
-      if (ns > 0) add_spec(sp.s[field][0], bidx, re, im);
-      if (ns > 1) add_spec(sp.s[field][1], bidx, re, im);
-      if (ns > 2) add_spec(sp.s[field][2], bidx, re, im);
+      if (ns > 0) add_spec(s0, bidx, re, im);
+      if (ns > 1) add_spec(s1, bidx, re, im);
+      if (ns > 2) add_spec(s2, bidx, re, im);
       return cx<R>{re, im};
     }
     return in[(base + j * bsa) * B3 + m];
@@ -197,6 +210,13 @@ __global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, 
     return;
   }
   const R sc = RT<R>::from(scale);
+  OutSpec<R> ore{}, oim{};
+#pragma unroll
+  for (int f = 0; f < BOX_MAXF; ++f)
+    if (f == field) {
+      ore = outs.re[f];
+      oim = outs.im[f];
+    }
   const int64_t gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1]);
   const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
   const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
@@ -206,8 +226,8 @@ __global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, 
     if (j >= nj) continue;
     const int bidx = (int)(gbase + (j0 + j) * gsa);
     const cx<R> v = cnorm(acc[j]);
-    box_store<R>(outs.re[field], bidx, m, B3, v.re * sc);
-    box_store<R>(outs.im[field], bidx, m, B3, v.im * sc);
+    box_store<R>(ore, bidx, m, B3, v.re * sc);
+    box_store<R>(oim, bidx, m, B3, v.im * sc);
   }
 }
 
@@ -252,8 +272,9 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
 }
 
 // ------------------------------------------------------------------ fused twiddle + local FFT + kernel
-// One CTA per K1 block: Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat[K1][.]; back.
-// Shared memory: B^3 complex with x rows padded to B+1.
+// One CTA per (K1 block, field): Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat[K1][.]; back.
+// The inverse runs as conj(FFT(conj(.))) so one FFT body serves all six axis passes (small code,
+// no instruction-cache stalls).  Shared memory: B^3 complex with x rows padded to B+1.
 template <int B>
 struct MidGeom {
   static constexpr int RS = B + 1;          // padded row
@@ -280,81 +301,59 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
     const cx<R> *tab = a == 0 ? twx : (a == 1 ? twy : twz);
     T[a][mm] = tab[(int)(((int64_t)mm * k1) % Pc)];
   }
+  __syncthreads();
   cx<R> *Yb = Y + blockIdx.y * fstride + kb * B3;  // field blockIdx.y
-  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
-    const int x = i % B, y = (i / B) % B, z = i / (B * B);
-    S[(z * B + y) * RS + x] = Yb[i];
+  // element-wise loops: thread t owns cells (x, y) = (t % B, t / B) of every z plane (B*B <= 256)
+  const int ex = threadIdx.x % B, ey = (threadIdx.x / B) % B;
+  const int zstep = blockDim.x / (B * B);
+  const int z0 = threadIdx.x / (B * B);
+  {
+    const cx<R> txy = cmul(T[0][ex], T[1][ey]);
+    for (int z = z0; z < B; z += zstep) {
+      const cx<R> w = cmul(txy, T[2][z]);
+      S[(z * B + ey) * RS + ex] = cmul(Yb[(z * B + ey) * B + ex], w);
+    }
   }
-  __syncthreads();
-  // forward: x lines with the full twiddle, then y, then z
-  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
-    const int y = line % B, z = line / B;
-    const cx<R> tyz = cmul(T[1][y], T[2][z]);
-    cx<R> v[B];
-#pragma unroll
-    for (int x = 0; x < B; ++x) v[x] = cmul(S[(z * B + y) * RS + x], cmul(T[0][x], tyz));
-    fft_reg<R, B, false>(v, tw);
-#pragma unroll
-    for (int x = 0; x < B; ++x) S[(z * B + y) * RS + x] = v[x];
-  }
-  __syncthreads();
-  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
-    const int x = line % B, z = line / B;
-    cx<R> v[B];
-#pragma unroll
-    for (int y = 0; y < B; ++y) v[y] = S[(z * B + y) * RS + x];
-    fft_reg<R, B, false>(v, tw);
-#pragma unroll
-    for (int y = 0; y < B; ++y) S[(z * B + y) * RS + x] = v[y];
-  }
-  __syncthreads();
-  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
-    const int x = line % B, y = line / B;
-    cx<R> v[B];
-#pragma unroll
-    for (int z = 0; z < B; ++z) v[z] = S[(z * B + y) * RS + x];
-    fft_reg<R, B, false>(v, tw);
-    if (MULTIPLY) {
-      // X[K1][K2] *= Ghat, K2 = (x, y, z) local frequency, then inverse z
-#pragma unroll
-      for (int z = 0; z < B; ++z) {
-        const R gk = Gh[kb * B3 + (z * B + y) * B + x];
-        v[z] = cx<R>{v[z].re * gk, v[z].im * gk};
+  const int npass = MULTIPLY ? 6 : 3;
+  for (int pass = 0; pass < npass; ++pass) {
+    __syncthreads();
+    if (pass == 3) {
+      // X *= Ghat (real), then conjugate: the inverse is conj(FFT(conj(X Ghat)))
+      for (int z = z0; z < B; z += zstep) {
+        cx<R> &v = S[(z * B + ey) * RS + ex];
+        const R gk = Gh[kb * B3 + (z * B + ey) * B + ex];
+        v = cx<R>{v.re * gk, -(v.im * gk)};
       }
-      fft_reg<R, B, true>(v, tw);
+      __syncthreads();
+    }
+    const int ax = pass % 3;
+    for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
+      const int l0 = line % B, l1 = line / B;
+      int base, stride;
+      if (ax == 0) base = (l1 * B + l0) * RS, stride = 1;             // x lines: (y, z) = (l0, l1)
+      else if (ax == 1) base = l1 * B * RS + l0, stride = RS;         // y lines: (x, z) = (l0, l1)
+      else base = l1 * RS + l0, stride = B * RS;                      // z lines: (x, y) = (l0, l1)
+      cx<R> v[B];
 #pragma unroll
-      for (int z = 0; z < B; ++z) S[(z * B + y) * RS + x] = v[z];
-    } else {
-      // kernel-spectrum generation: store the real part of X (G even => X real)
+      for (int i = 0; i < B; ++i) v[i] = S[base + i * stride];
+      fft_reg<R, B, false>(v, tw);
+      if (!MULTIPLY && ax == 2) {
+        // kernel-spectrum generation: store the real part (G even => X real); l0 = x, l1 = y
 #pragma unroll
-      for (int z = 0; z < B; ++z) kout[kb * B3 + (z * B + y) * B + x] = v[z].re;
+        for (int i = 0; i < B; ++i) kout[kb * B3 + (i * B + l1) * B + l0] = v[i].re;
+      } else {
+#pragma unroll
+        for (int i = 0; i < B; ++i) S[base + i * stride] = v[i];
+      }
     }
   }
   if (!MULTIPLY) return;
   __syncthreads();
-  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
-    const int x = line % B, z = line / B;
-    cx<R> v[B];
-#pragma unroll
-    for (int y = 0; y < B; ++y) v[y] = S[(z * B + y) * RS + x];
-    fft_reg<R, B, true>(v, tw);
-#pragma unroll
-    for (int y = 0; y < B; ++y) S[(z * B + y) * RS + x] = v[y];
-  }
-  __syncthreads();
-  for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
-    const int y = line % B, z = line / B;
-    const cx<R> tyz = conj(cmul(T[1][y], T[2][z]));
-    cx<R> v[B];
-#pragma unroll
-    for (int x = 0; x < B; ++x) v[x] = S[(z * B + y) * RS + x];
-    fft_reg<R, B, true>(v, tw);
-#pragma unroll
-    for (int x = 0; x < B; ++x) S[(z * B + y) * RS + x] = cmul(v[x], cmul(conj(T[0][x]), tyz));
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < B3; i += blockDim.x) {
-    const int x = i % B, y = (i / B) % B, z = i / (B * B);
-    Yb[i] = S[(z * B + y) * RS + x];
+  {
+    const cx<R> txy = conj(cmul(T[0][ex], T[1][ey]));
+    for (int z = z0; z < B; z += zstep) {
+      const cx<R> w = cmul(txy, conj(T[2][z]));
+      Yb[(z * B + ey) * B + ex] = cmul(conj(S[(z * B + ey) * RS + ex]), w);
+    }
   }
 }
