@@ -68,92 +68,11 @@ struct FwdSpecs {   // per field: up to three input specs (first forward pass on
   int n[BOX_MAXF];
 };
 
-// ------------------------------------------------------------------ block-index DFT, forward
-// Pass along axis `ax`: for every line (the two other block coordinates within `ext`) and every
-// local cell m, out[.. k ..][m] = sum_{j < nb} W_P^{j k} in[.. j ..][m], k < P.  grid.z = 2 * field +
-// half: each CTA produces the even (half 0) or odd (half 1) outputs k of one field.  The first pass
-// (gather != 0) reads its input through the field's specs instead of `in`.  Field f's arrays start at
-// in + f * fstride, out + f * fstride.
-template <class R, int B>
-__global__ void __launch_bounds__(256) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
-                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
-                                                  int gather, FwdSpecs sp) {
-  constexpr int B3 = B * B * B;
-  const int nb = g.nb[ax];
-  const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
-  const int e1 = ax == 0 ? ext.y : ext.x;
-  const int64_t line = blockIdx.y;
-  const int l1 = (int)(line % e1), l2 = (int)(line / e1);
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int field = blockIdx.z >> 1, half = blockIdx.z & 1;
-  if (m >= B3) return;
-  in += field * fstride;
-  out += field * fstride;
-  // addresses along the pass axis: box array element (base + j * bsa) * B3 + m, gather index gbase + j * gsa
-  const int64_t bsa = g.bs[ax];
-  const int64_t base = (int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2];
-  const int64_t gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1]);
-  const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
-  const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
-  const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
-  // per-field specs copied with compile-time indices (a dynamic index would copy the parameter block
-  // to local memory)
-  InSpec s0{}, s1{}, s2{};
-  int ns = 0;
-  if (gather) {
-#pragma unroll
-    for (int f = 0; f < BOX_MAXF; ++f)
-      if (f == field) {
-        s0 = sp.s[f][0];
-        s1 = sp.s[f][1];
-        s2 = sp.s[f][2];
-        ns = sp.n[f];
-      }
-  }
-  auto add_spec = [&](const InSpec &s, int64_t bidx, R &re, R &im) {
-    const int idx = s.gather[bidx];
-    if (idx < 0) return;
-    const int64_t e = (int64_t)idx * B3 + m;
-    if (s.mask && !(s.mask[e] & s.bits)) return;
-    const R v = load_field<R>(s.src, e, s.dtype);
-    if (s.part) im = im + v;
-    else re = re + v;
-  };
-  auto elem_in = [&](int j) -> cx<R> {
-    if (gather) {
-      const int64_t bidx = gbase + j * gsa;
-      R re = RT<R>::zero(), im = RT<R>::zero();
-      if (ns > 0) add_spec(s0, bidx, re, im);
-      if (ns > 1) add_spec(s1, bidx, re, im);
-      if (ns > 2) add_spec(s2, bidx, re, im);
-      return cx<R>{re, im};
-    }
-    return in[(base + j * bsa) * B3 + m];
-  };
-  const int P = 2 * nb;
-  cx<R> acc[BOX_NB_MAX];
-#pragma unroll
-  for (int k = 0; k < BOX_NB_MAX; ++k) acc[k] = cx_zero<R>();
-  for (int j = 0; j < nb; ++j) {
-    const cx<R> x = elem_in(j);
-    int n = half ? j : 0;  // (j * (2k + half)) mod P for k = 0, 1, ...
-    const int step = (2 * j) % P;
-#pragma unroll
-    for (int k = 0; k < BOX_NB_MAX; ++k) {
-      if (k < nb) acc[k] = n ? cmac_lazy(acc[k], x, tw.w[n]) : cadd(acc[k], x);
-      n += step;
-      if (n >= P) n -= P;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < BOX_NB_MAX; ++k)
-    if (k < nb) out[(base + (int64_t)(2 * k + half) * bsa) * B3 + m] = cnorm(acc[k]);
-}
+template <class R>
+struct InvOuts {  // per field: destinations of the real and imaginary parts (last inverse pass)
+  OutSpec<R> re[BOX_MAXF], im[BOX_MAXF];
+};
 
-// ------------------------------------------------------------------ block-index DFT, inverse
-// out[.. j ..][m] = sum_{k < P} W_P^{-j k} in[.. k ..][m] for j < nb (unnormalised).  grid.z =
-// 2 * field + part: part 0 computes outputs j < ceil(nb/2), part 1 the rest.  The last pass
-// (final != 0) writes scale * re and scale * im through the field's output specs instead of `out`.
 template <class R>
 LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
   if (!o.scatter) return;
@@ -165,69 +84,120 @@ LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
   store_field<R>(o.dst, o.off + (int64_t)ob * B3 + m, o.dtype, v);
 }
 
-template <class R>
-struct InvOuts {  // per field: destinations of the real and imaginary parts (last inverse pass)
-  OutSpec<R> re[BOX_MAXF], im[BOX_MAXF];
-};
-
-template <class R, int B>
-__global__ void __launch_bounds__(256) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
-                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
-                                                  int final, InvOuts<R> outs, double scale) {
+// ------------------------------------------------------------------ block-index DFTs
+// Pass along axis `ax`: for every line (the two other block coordinates within `ext`) and every local
+// cell m:
+//   forward  out[.. k ..][m] = sum_{j < nb}  W_P^{ j k} in[.. j ..][m],   k < P = 2 nb
+//   inverse  out[.. j ..][m] = sum_{k < P}   W_P^{-j k} in[.. k ..][m],   j < nb (unnormalised)
+// A thread owns CELLS cells (m, m + 256, ...) and a chunk of at most CH consecutive outputs;
+// grid = (B^3 / (256 CELLS), lines, field * nchunk + chunk).  The first forward pass (gather) reads
+// through the field's input specs, the last inverse pass (final) writes through its output specs.
+// Field f's arrays start at in + f * fstride, out + f * fstride.
+template <class R, int B, int CH, int CELLS>
+__global__ void __launch_bounds__(256) k_bdft(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
+                                              int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
+                                              int inverse, int gather, int final, int nchunk, FwdSpecs sp,
+                                              InvOuts<R> outs, double scale) {
   constexpr int B3 = B * B * B;
   const int nb = g.nb[ax];
+  const int P = 2 * nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
-  const int64_t line = blockIdx.y;
-  const int l1 = (int)(line % e1), l2 = (int)(line / e1);
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int field = blockIdx.z >> 1, part = blockIdx.z & 1;
-  if (m >= B3) return;
-  in += field * fstride;
-  out += field * fstride;
-  const int nh = (nb + 1) >> 1;
-  const int j0 = part ? nh : 0, nj = part ? nb - nh : nh;
-  const int64_t bsa = g.bs[ax];
-  const int64_t base = (int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2];
-  const int P = 2 * nb;
-  cx<R> acc[(BOX_NB_MAX + 1) / 2];
-#pragma unroll
-  for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j) acc[j] = cx_zero<R>();
-  for (int k = 0; k < P; ++k) {
-    const cx<R> x = in[(base + k * bsa) * B3 + m];
-    int n = (j0 * k) % P;  // (j * k) mod P for j = j0, j0 + 1, ...
-#pragma unroll
-    for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j) {
-      if (j < nj) acc[j] = n ? cmac_lazy(acc[j], x, conj(tw.w[n])) : cadd(acc[j], x);
-      n += k;
-      if (n >= P) n -= P;
-    }
-  }
-  if (!final) {
-#pragma unroll
-    for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j)
-      if (j < nj) out[(base + (int64_t)(j0 + j) * bsa) * B3 + m] = cnorm(acc[j]);
-    return;
-  }
-  const R sc = RT<R>::from(scale);
+  const int line = blockIdx.y;
+  const int l1 = line % e1, l2 = line / e1;
+  const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
+  const int nout = inverse ? nb : P, nin = inverse ? P : nb;
+  const int o0 = chunk * CH;
+  const int no = nout - o0 < CH ? nout - o0 : CH;
+  const int m0 = blockIdx.x * (256 * CELLS) + threadIdx.x;
+  const int64_t bsa = g.bs[ax] * (int64_t)B3;  // element stride along the pass axis
+  const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
+  // gather / scatter block indices: box block (x, y, z) -> (z * nby + y) * nbx + x
+  const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
+  const int gs1 = a1 == 0 ? 1 : g.nb[0];
+  const int gs2 = a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1];
+  const int gbase = l1 * gs1 + l2 * gs2;
+  InSpec s0{}, s1{}, s2{};
+  int ns = 0;
   OutSpec<R> ore{}, oim{};
 #pragma unroll
   for (int f = 0; f < BOX_MAXF; ++f)
     if (f == field) {
-      ore = outs.re[f];
-      oim = outs.im[f];
+      if (gather) {
+        s0 = sp.s[f][0];
+        s1 = sp.s[f][1];
+        s2 = sp.s[f][2];
+        ns = sp.n[f];
+      }
+      if (final) {
+        ore = outs.re[f];
+        oim = outs.im[f];
+      }
     }
-  const int64_t gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1]);
-  const int64_t gs1 = a1 == 0 ? 1 : g.nb[0];
-  const int64_t gs2 = a2 == 1 ? g.nb[0] : (int64_t)g.nb[0] * g.nb[1];
-  const int64_t gbase = (int64_t)l1 * gs1 + (int64_t)l2 * gs2;
+  const cx<R> *src = in + field * fstride + lbase;
+  cx<R> acc[CELLS][CH];
 #pragma unroll
-  for (int j = 0; j < (BOX_NB_MAX + 1) / 2; ++j) {
-    if (j >= nj) continue;
-    const int bidx = (int)(gbase + (j0 + j) * gsa);
-    const cx<R> v = cnorm(acc[j]);
-    box_store<R>(ore, bidx, m, B3, v.re * sc);
-    box_store<R>(oim, bidx, m, B3, v.im * sc);
+  for (int c = 0; c < CELLS; ++c)
+#pragma unroll
+    for (int k = 0; k < CH; ++k) acc[c][k] = cx_zero<R>();
+  for (int j = 0; j < nin; ++j) {
+    cx<R> x[CELLS];
+    if (gather) {
+      const int bidx = gbase + j * gsa;
+#pragma unroll
+      for (int c = 0; c < CELLS; ++c) {
+        const int m = m0 + 256 * c;
+        R re = RT<R>::zero(), im = RT<R>::zero();
+        auto add = [&](const InSpec &q) {
+          const int idx = q.gather[bidx];
+          if (idx < 0) return;
+          const int64_t e = (int64_t)idx * B3 + m;
+          if (q.mask && !(q.mask[e] & q.bits)) return;
+          const R v = load_field<R>(q.src, e, q.dtype);
+          if (q.part) im = im + v;
+          else re = re + v;
+        };
+        if (ns > 0) add(s0);
+        if (ns > 1) add(s1);
+        if (ns > 2) add(s2);
+        x[c] = cx<R>{re, im};
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CELLS; ++c) x[c] = src[j * bsa + m0 + 256 * c];
+    }
+    int n = (int)(((int64_t)j * o0) % P);  // (j * k) mod P for k = o0, o0 + 1, ...
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      if (k < no) {
+        const cx<R> w = inverse ? conj(tw.w[n]) : tw.w[n];
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) acc[c][k] = n ? cmac_lazy(acc[c][k], x[c], w) : cadd(acc[c][k], x[c]);
+      }
+      n += j;
+      if (n >= P) n -= P;
+    }
+  }
+  if (!final) {
+    cx<R> *dst = out + field * fstride + lbase;
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (k < no)
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) dst[(o0 + k) * bsa + m0 + 256 * c] = cnorm(acc[c][k]);
+    return;
+  }
+  const R sc = RT<R>::from(scale);
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    if (k >= no) continue;
+    const int bidx = gbase + (o0 + k) * gsa;
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+      const cx<R> v = cnorm(acc[c][k]);
+      box_store<R>(ore, bidx, m0 + 256 * c, B3, v.re * sc);
+      box_store<R>(oim, bidx, m0 + 256 * c, B3, v.im * sc);
+    }
   }
 }
 

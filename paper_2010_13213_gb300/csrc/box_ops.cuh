@@ -68,7 +68,6 @@ static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec
   const int *nb = g.nb, *P = g.P;
   const int64_t nblk = (int64_t)P[0] * P[1] * P[2];
   const int64_t fstride = nblk * B3;
-  const unsigned gx = (B3 + 255) / 256;
   const size_t sm = sizeof(cx<R>) * (size_t)B * B * (B + 1);
   static bool attr = false;
   if (!attr) {
@@ -85,26 +84,32 @@ static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec
       outs.re[f] = ore[f0 + f];
       outs.im[f] = oim[f0 + f];
     }
-    const unsigned zf = 2 * n;
-    // forward x (gather), y, z
-    k_bdft_fwd<R, B><<<dim3(gx, nb[1] * nb[2], zf), 256, 0, st>>>(nullptr, Y0, fstride, g, 0,
-                                                                  make_int3(0, nb[1], nb[2]), btw_of<R>(S, 0), 1, sp);
-    k_bdft_fwd<R, B><<<dim3(gx, P[0] * nb[2], zf), 256, 0, st>>>(Y0, Y1, fstride, g, 1, make_int3(P[0], 0, nb[2]),
-                                                                 btw_of<R>(S, 1), 0, sp);
-    k_bdft_fwd<R, B><<<dim3(gx, P[0] * P[1], zf), 256, 0, st>>>(Y1, Y0, fstride, g, 2, make_int3(P[0], P[1], 0),
-                                                                btw_of<R>(S, 2), 0, sp);
+    // forward x (gather), y, z; mid; inverse z, y, x (scatter)
+    auto pass = [&](const cx<R> *in_, cx<R> *out_, int ax, int3 ext, int lines, int inverse, int gather,
+                    int final, double sc) {
+      const int nb_ax = nb[ax];
+      const int nout = inverse ? nb_ax : 2 * nb_ax;
+      if (nout <= 8) {
+        const int nch = 1;
+        k_bdft<R, B, 8, 2><<<dim3((B3 + 511) / 512, lines, n * nch), 256, 0, st>>>(
+            in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), inverse, gather, final, nch, sp, outs, sc);
+      } else {
+        const int nch = (nout + 7) / 8;
+        k_bdft<R, B, 8, 1><<<dim3((B3 + 255) / 256, lines, n * nch), 256, 0, st>>>(
+            in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), inverse, gather, final, nch, sp, outs, sc);
+      }
+    };
+    pass(nullptr, Y0, 0, make_int3(0, nb[1], nb[2]), nb[1] * nb[2], 0, 1, 0, 1.0);
+    pass(Y0, Y1, 1, make_int3(P[0], 0, nb[2]), P[0] * nb[2], 0, 0, 0, 1.0);
+    pass(Y1, Y0, 2, make_int3(P[0], P[1], 0), P[0] * P[1], 0, 0, 0, 1.0);
     if (mark) mark(mark_ctx, 2);
     k_box_mid<R, B, true><<<dim3((unsigned)nblk, n), 256, sm, st>>>(Y0, fstride, spec_of<R>(S), g, tw_of<R>(S, 0),
                                                                    tw_of<R>(S, 1), tw_of<R>(S, 2), make_tw64<R>(),
                                                                    nullptr);
     if (mark) mark(mark_ctx, 3);
-    k_bdft_inv<R, B><<<dim3(gx, P[0] * P[1], zf), 256, 0, st>>>(Y0, Y1, fstride, g, 2, make_int3(P[0], P[1], 0),
-                                                                btw_of<R>(S, 2), 0, outs, 1.0);
-    k_bdft_inv<R, B><<<dim3(gx, P[0] * nb[2], zf), 256, 0, st>>>(Y1, Y0, fstride, g, 1, make_int3(P[0], 0, nb[2]),
-                                                                 btw_of<R>(S, 1), 0, outs, 1.0);
-    k_bdft_inv<R, B><<<dim3(gx, nb[1] * nb[2], zf), 256, 0, st>>>(Y0, Y1, fstride, g, 0,
-                                                                  make_int3(0, nb[1], nb[2]), btw_of<R>(S, 0), 1,
-                                                                  outs, scale);
+    pass(Y0, Y1, 2, make_int3(P[0], P[1], 0), P[0] * P[1], 1, 0, 0, 1.0);
+    pass(Y1, Y0, 1, make_int3(P[0], 0, nb[2]), P[0] * nb[2], 1, 0, 0, 1.0);
+    pass(Y0, Y1, 0, make_int3(0, nb[1], nb[2]), nb[1] * nb[2], 1, 0, 1, scale);
     if (mark) mark(mark_ctx, 4);
   }
   cudaError_t e = cudaGetLastError();
