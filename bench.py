@@ -31,7 +31,7 @@ METRIC = "Poisson-solve Mcells/s, mixed vs FP64 at rel err ≤1e-10; % of HBM ro
 WORKLOAD = "vortex-ring vector Poisson, R=1, sigma=0.2R, h=R/32, 96x96x48 cells, 16^3 blocks, 3 comps"
 FP32_INST_PEAK = 152 * 128 * 2.070e9  # FP32 lanes x SMs x max SM clock (instructions/s)
 FP64_FLOP_PEAK = 1.25e12              # nominal dense FP64 of GB300
-DF_OPS_PER_CMAC = 72                  # FP32 instructions of one double-float complex multiply-add
+DF_OPS_PER_CMAC = 54                  # FP32 instructions of one renormalised double-float complex multiply-add
 
 
 def _env_rank():
@@ -106,28 +106,42 @@ def _phases(ph):
     return {n: float(v) for n, v in zip(PHASE_NAMES, ph) if v}
 
 
-def df_box_instructions(B, nb, nfields):
-    """FP32 instructions the double-float block-index FFT mode needs per solve (algorithmic count).
+CMAC, CADD, CNORM, CMUL, DFMUL = 48, 16, 6, 38, 7  # FP32 instructions of the double-float ops (common.cuh)
 
-    Block-index DFTs: every complex multiply-add is 72 FP32 instructions (4 TwoProd-based products
-    of 7 and 4 renormalised sums of 11 -- see common.cuh); per field the forward passes do
-    2 nb_a^2 products per line and cell, the inverse P_a nb_a.  Local FFTs: radix-2 B-point FFT =
-    (B/2) log2 B butterflies with B log2 B - ... twiddled products; per B^3 block six axis passes of
-    B^2 lines, plus the four-step twiddles (2 complex products per cell each way) and the real
-    kernel product (2 double-float products per cell).
-    """
+
+def _dft_pass_inst(P, nin, nout, lines, B3, double_first=False):
+    """One block-index DFT pass: every (input j, output k) pair is a multiply-add unless W^{jk} = 1."""
+    per = sum((CADD if (j * k) % P == 0 else CMAC) for j in range(nin) for k in range(nout)) + nout * CNORM
+    if double_first:  # real-field inverse x pass doubles the interior inputs (one lazy add each)
+        per += max(nin - 2, 0) * CADD
+    return lines * B3 * per
+
+
+def df_box_instructions(B, nb, ncomp):
+    """FP32 instructions the double-float block-index FFT mode executes per solve, counted from the
+    arithmetic of the kernels (not measured): block-index DFT passes (k_bdft) and the fused local-FFT
+    kernel (k_box_mid).  Components ride two per complex field; an odd last component is a real field
+    kept on the Hermitian half K1x <= Px/2."""
     import math
     nx, ny, nz = nb
     px, py, pz = 2 * nx, 2 * ny, 2 * nz
     B3 = B ** 3
-    fwd = B3 * (ny * nz * 2 * nx * nx + px * nz * 2 * ny * ny + px * py * 2 * nz * nz)
-    inv = B3 * (px * py * pz * nz + px * nz * py * ny + ny * nz * px * nx)
-    dft = (fwd + inv) * 72
     lg = int(math.log2(B))
     twiddled = sum((B // ln) * (ln // 2 - 1) for ln in [2 ** s for s in range(1, lg + 1)])
-    fft1d = twiddled * 50 + (B // 2) * lg * 2 * 22
-    local = px * py * pz * (6 * B * B * fft1d + 4 * B3 * 50 + B3 * 2 * 7)
-    return nfields * dft, nfields * local
+    fft1d = twiddled * CMUL + (B // 2) * lg * 2 * CADD + B * CNORM
+    mid_block = 6 * B * B * fft1d + 2 * B3 * 2 * CMUL + B3 * 2 * DFMUL
+    dft = mid = 0
+    fields = [px] * (ncomp // 2) + [px // 2 + 1] * (ncomp % 2)
+    for pxu in fields:
+        real = pxu < px
+        dft += _dft_pass_inst(px, nx, pxu, ny * nz, B3)                    # forward x
+        dft += _dft_pass_inst(py, ny, py, pxu * nz, B3)                    # forward y
+        dft += _dft_pass_inst(pz, nz, pz, pxu * py, B3)                    # forward z
+        dft += _dft_pass_inst(pz, pz, nz, pxu * py, B3)                    # inverse z
+        dft += _dft_pass_inst(py, py, ny, pxu * nz, B3)                    # inverse y
+        dft += _dft_pass_inst(px, pxu, nx, ny * nz, B3, double_first=real)  # inverse x
+        mid += pxu * py * pz * mid_block
+    return dft, mid
 
 
 def roofline_entry(case, B, ncomp, rep, ph):
@@ -140,12 +154,12 @@ def roofline_entry(case, B, ncomp, rep, ph):
         kern, launches = "k_mac_pair<df,4,3> (block-pair multiply-accumulate)", 1
     else:
         nz, ny, nx = (n // B for n in case["shape"])
-        nfields = (ncomp + 1) // 2
-        dft, local = df_box_instructions(B, (nx, ny, nz), nfields)
+        ngroups = (1 if ncomp // 2 else 0) + (1 if ncomp % 2 else 0)
+        dft, local = df_box_instructions(B, (nx, ny, nz), ncomp)
         if ph[3] >= ph[2] + ph[4]:
-            inst, ms, kern, launches = local, ph[3], "k_box_mid<df,16> (twiddle + local FFT + kernel + inverse)", nfields
+            inst, ms, kern, launches = local, ph[3], "k_box_mid<df,16> (twiddle + local FFT + kernel + inverse)", ngroups
         else:
-            inst, ms, kern, launches = dft, ph[2] + ph[4], "k_bdft_fwd/inv<df,16> (block-index DFTs)", 6 * nfields
+            inst, ms, kern, launches = dft, ph[2] + ph[4], "k_bdft<df,16> (block-index DFT passes)", 6 * ngroups
     ach = inst / (ms * 1e-3)
     return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": FP32_INST_PEAK / 1e12,
             "unit": "T FP32-inst/s", "frac": ach / FP32_INST_PEAK, "traffic": None,

@@ -32,6 +32,7 @@ struct BoxGeom {
   int nb[3];    // box blocks per axis
   int P[3];     // 2 nb
   int64_t bs[3];  // block strides (in blocks) of the full P-array: 1, Px, Px*Py
+  int pxu;      // block frequencies K1x kept: Px, or Px/2 + 1 for a real field (Hermitian symmetry)
 };
 
 // Source of the first forward pass: box block -> buffer block (gather, -1 = absent), a field
@@ -106,7 +107,10 @@ __global__ void __launch_bounds__(256) k_bdft(const cx<R> *__restrict__ in, cx<R
   const int line = blockIdx.y;
   const int l1 = line % e1, l2 = line / e1;
   const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
-  const int nout = inverse ? nb : P, nin = inverse ? P : nb;
+  // a real field keeps K1x in [0, Px/2] only: the forward x pass stops there and the inverse x pass
+  // folds the missing half in as the conjugate (weights 1, 2, ..., 2, 1 on the real part)
+  const bool realx = ax == 0 && g.pxu < P;
+  const int nout = inverse ? nb : (realx ? g.pxu : P), nin = inverse ? (realx ? g.pxu : P) : nb;
   const int o0 = chunk * CH;
   const int no = nout - o0 < CH ? nout - o0 : CH;
   const int m0 = blockIdx.x * (256 * CELLS) + threadIdx.x;
@@ -166,6 +170,9 @@ __global__ void __launch_bounds__(256) k_bdft(const cx<R> *__restrict__ in, cx<R
 #pragma unroll
       for (int c = 0; c < CELLS; ++c) x[c] = src[j * bsa + m0 + 256 * c];
     }
+    if (realx && inverse && j != 0 && 2 * j != P)
+#pragma unroll
+      for (int c = 0; c < CELLS; ++c) x[c] = cx<R>{x[c].re + x[c].re, x[c].im + x[c].im};
     int n = (int)(((int64_t)j * o0) % P);  // (j * k) mod P for k = o0, o0 + 1, ...
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(256) k_bdft(const cx<R> *__restrict__ in, cx<R
     for (int c = 0; c < CELLS; ++c) {
       const cx<R> v = cnorm(acc[c][k]);
       box_store<R>(ore, bidx, m0 + 256 * c, B3, v.re * sc);
-      box_store<R>(oim, bidx, m0 + 256 * c, B3, v.im * sc);
+      if (!realx) box_store<R>(oim, bidx, m0 + 256 * c, B3, v.im * sc);
     }
   }
 }
@@ -261,8 +268,10 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
   extern __shared__ unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
   __shared__ cx<R> T[3][B];
-  const int64_t kb = blockIdx.x;  // K1 block, linear in the full P array
-  const int k1x = (int)(kb % g.P[0]), k1y = (int)((kb / g.P[0]) % g.P[1]), k1z = (int)(kb / ((int64_t)g.P[0] * g.P[1]));
+  // K1 block: blockIdx.x runs over K1x < pxu (all of Px, or Px/2 + 1 for a real field)
+  const int k1x = (int)(blockIdx.x % g.pxu), k1y = (int)((blockIdx.x / g.pxu) % g.P[1]);
+  const int k1z = (int)(blockIdx.x / ((unsigned)g.pxu * g.P[1]));
+  const int64_t kb = k1x + (int64_t)g.P[0] * (k1y + (int64_t)g.P[1] * k1z);  // linear in the full P array
   const int Pcx = g.P[0] * B, Pcy = g.P[1] * B, Pcz = g.P[2] * B;
   if (threadIdx.x < 3 * B) {
     const int a = threadIdx.x / B, mm = threadIdx.x % B;
