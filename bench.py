@@ -234,24 +234,26 @@ def run_gpu(args):
 
     mode = {"auto": L.LGF_MAC_AUTO, "pair": L.LGF_MAC_PAIR, "box": L.LGF_MAC_BOX}[args.mode]
 
-    def solve(prec, rep=None, timing=0, fin=f, fout=phi, m=None):
+    def solve(prec, rep=None, timing=0, fin=f, fout=phi, m=None, slices=0):
         L.lgf_poisson_solve(table, mesh, ncomp, fin.data_ptr(), fout.data_ptr(), L.LGF_F64,
-                            L.make_opts(precision=prec, mac_mode=mode if m is None else m, timing=timing), rep,
-                            stream)
+                            L.make_opts(precision=prec, mac_mode=mode if m is None else m, timing=timing,
+                                        dft_slices=slices), rep, stream)
 
     # accuracy outside the timed region: against the oracle (rank 0 computes, all ranks check)
     ref = cpu_oracle_step(case)
     import lgf_synth as S
     errs = {}
-    for name, prec in (("fp64", L.LGF_PREC_FP64), ("df32", L.LGF_PREC_DF32), ("fp32", L.LGF_PREC_FP32)):
-        solve(prec)
+    for name, prec, sl in (("fp64", L.LGF_PREC_FP64, 0), ("df32", L.LGF_PREC_DF32, 0), ("fp32", L.LGF_PREC_FP32, 0),
+                           ("df32_tc5", L.LGF_PREC_DF32, 5), ("df32_tc6", L.LGF_PREC_DF32, 6),
+                           ("fp32_tc3", L.LGF_PREC_FP32, 3)):
+        solve(prec, slices=sl)
         torch.cuda.synchronize()
         got = S.blocks_to_box(phi.cpu().numpy(), case["blocks"], B, case["shape"])
         errs[name] = float(max(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max() for c in range(2)))
 
-    def timed(prec, m=None):
+    def timed(prec, m=None, slices=0):
         for _ in range(args.warmup):
-            solve(prec, m=m)
+            solve(prec, m=m, slices=slices)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -260,7 +262,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1.0)  # L2 flush between timed steps (256 MiB write), outside the events
-            solve(prec, rep, timing=1, m=m)
+            solve(prec, rep, timing=1, m=m, slices=slices)
             step_ms.append(rep.ms_total)
             phase_ms.append([rep.ms_phase[i] for i in range(8)])
         torch.cuda.synchronize()
@@ -274,6 +276,8 @@ def run_gpu(args):
         ms_64, ph_64, wall_64, rep_64 = timed(L.LGF_PREC_FP64)
         ms_32, ph_32, wall_32, rep_32 = timed(L.LGF_PREC_FP32)
         ms_dfp, ph_dfp, _, rep_dfp = timed(L.LGF_PREC_DF32, m=L.LGF_MAC_PAIR)
+        tc = {name: timed(prec, slices=sl) for name, prec, sl in
+              (("df32_tc5", L.LGF_PREC_DF32, 5), ("df32_tc6", L.LGF_PREC_DF32, 6), ("fp32_tc3", L.LGF_PREC_FP32, 3))}
     clocks = clk.summary()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -327,6 +331,8 @@ def run_gpu(args):
                  "rel_err": errs["fp32"], "note": "plain FP32: error above the 1e-10 target, reported only"},
         "df32_pair_mode": {"value": cells * world / (ms_dfp * 1e-3) / 1e6, "unit": "Mcells/s",
                            "ms_per_step": ms_dfp, "phases_ms": _phases(ph_dfp)},
+        "dft_gemm": {name: {"value": cells * world / (v[0] * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": v[0],
+                            "rel_err": errs[name], "phases_ms": _phases(v[1])} for name, v in tc.items()},
         "mode": MODE_NAMES[rep_df.mac_mode_used],
         "phases_ms_df32": _phases(ph_df),
         "table_build_s": t_tab,

@@ -96,6 +96,14 @@ typedef struct lgf_solve_opts {
   int32_t residual;      /* 1: compute the FP64 residual into the report (synchronises) */
   int32_t timing;        /* 1: time the phases with CUDA events into the report (synchronises) */
   double residual_tol;   /* > 0 with residual = 1: LGF_E_PRECISION when residual_rel exceeds it */
+  int32_t dft_slices;    /* 0: block-index DFT passes on the CUDA cores.  S > 0: those passes run as
+                            tensor-core GEMMs (BF16 operands, FP32 accumulation) with S split-precision
+                            digit slices per operand, exact per slice level and recombined in the
+                            solve's arithmetic: FP32 takes S = 1..3 (1 = plain BF16), DF32 S = 4..6
+                            (relative error of a pass about 2^-(7+8(S-1)) of each cell line's largest
+                            value).  BOX mode only (AUTO picks BOX where the level allows it); FP64
+                            rejects S > 0 with LGF_E_UNSUPPORTED. */
+  int32_t reserved;      /* 0 */
 } lgf_solve_opts;
 
 typedef struct lgf_report {
@@ -173,6 +181,13 @@ int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void
 int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev,
                    void *g_dev, int32_t dtype, double alpha_finest, const lgf_solve_opts *opts,
                    lgf_report *rep, void *cuda_stream);
+
+/*
+ * lgf_device_status -- synchronise the device and read the table's device status word: LGF_E_TIMEOUT
+ * (and the word cleared) when a bounded device-side wait of a kernel that used this table gave up since
+ * the last read, else LGF_OK.  Solves with opts->timing or opts->residual set read it themselves.
+ */
+int lgf_device_status(lgf_table *t);
 
 /* ---- batches: many independent instances solved as one unit, capturable into a CUDA graph */
 typedef struct lgf_batch lgf_batch; /* opaque */

@@ -77,7 +77,38 @@ int check_mesh(const lgf_mesh *m, int B_expected) {
 
 using namespace lgf;
 
+namespace lgf {
+
+int check_slices(const lgf_solve_opts &o) {
+  if (o.dft_slices == 0) return LGF_OK;
+  if (o.dft_slices < 0 || o.dft_slices > TC_SMAX) return set_error(LGF_E_INVALID_ARG, "dft_slices %d", o.dft_slices);
+  if (o.precision == LGF_PREC_FP64)
+    return set_error(LGF_E_UNSUPPORTED, "the tensor-core DFT-GEMM serves the FP32 and DF32 precisions");
+  if (o.precision == LGF_PREC_FP32 && o.dft_slices > 3)
+    return set_error(LGF_E_INVALID_ARG, "FP32 takes 1..3 DFT-GEMM slices (got %d)", o.dft_slices);
+  if (o.precision == LGF_PREC_DF32 && o.dft_slices < 4)
+    return set_error(LGF_E_INVALID_ARG, "DF32 takes 4..6 DFT-GEMM slices (got %d)", o.dft_slices);
+  return LGF_OK;
+}
+
+int take_device_status(lgf_table *t) {
+  int v = 0;
+  if (cudaMemcpy(&v, t->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_error(LGF_E_CUDA, "status word read failed");
+  if (!v) return LGF_OK;
+  cudaMemset(t->d_status, 0, sizeof(int));
+  return set_error(LGF_E_TIMEOUT, "a bounded device-side wait gave up (tensor-core DFT-GEMM)");
+}
+
+}  // namespace lgf
+
 extern "C" {
+
+int lgf_device_status(lgf_table *t) {
+  if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");
+  if (cudaDeviceSynchronize() != cudaSuccess) return set_error(LGF_E_CUDA, "device synchronisation failed");
+  return take_device_status(t);
+}
 
 const char *lgf_last_error(void) { return g_last_error.c_str(); }
 const char *lgf_version(void) { return "lgf-gb300 0.1 (sm_103a)"; }
@@ -94,6 +125,12 @@ int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_off
   cudaStream_t st = (cudaStream_t)cuda_stream;
   lgf_table *t = new lgf_table();
   cudaGetDevice(&t->device);
+  if (cudaMalloc(&t->d_status, sizeof(int)) != cudaSuccess || cudaMemset(t->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(t->d_status);
+    delete t;
+    return set_error(LGF_E_OOM, "status word");
+  }
   t->B = block;
   t->mo = make_int3(max_block_offset[0], max_block_offset[1], max_block_offset[2]);
   t->noff = (2 * t->mo.x + 1) * (2 * t->mo.y + 1) * (2 * t->mo.z + 1);
@@ -102,6 +139,7 @@ int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_off
   t->flags = flags;
   int rc = build_lgf_octant(t->N, &t->Gd, st, &t->quad_T, &t->quad_nodes);
   if (rc) {
+    cudaFree(t->d_status);
     delete t;
     return rc;
   }
@@ -132,6 +170,7 @@ int lgf_table_destroy(lgf_table *t) {
   if (!t) return LGF_OK;
   cudaDeviceSynchronize();
   if (t->Gd) cudaFree(t->Gd);
+  if (t->d_status) cudaFree(t->d_status);
   if (t->s64) cudaFree(t->s64);
   if (t->s32) cudaFree(t->s32);
   if (t->sdf) cudaFree(t->sdf);
@@ -165,10 +204,11 @@ int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void
   if (!f_dev || !phi_dev) return set_error(LGF_E_INVALID_ARG, "field pointer NULL");
   if (f_dev == phi_dev) return set_error(LGF_E_INVALID_ARG, "f and phi alias");
   if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
-  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0};
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0, 0, 0};
   if (opts) o = *opts;
   if (o.precision < 0 || o.precision > 2) return set_error(LGF_E_INVALID_ARG, "precision %d", o.precision);
   if (o.mac_mode < 0 || o.mac_mode > 2) return set_error(LGF_E_INVALID_ARG, "mac_mode %d", o.mac_mode);
+  if ((rc = check_slices(o))) return rc;
   if (rep) memset(rep, 0, sizeof(*rep));
   return solve_poisson(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream);
 }
@@ -184,7 +224,7 @@ int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f
   if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
   if (!(alpha_finest >= 0.0) || alpha_finest > 1e4)
     return set_error(LGF_E_INVALID_ARG, "alpha_finest %g", alpha_finest);
-  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0};
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0, 0, 0};
   if (opts) o = *opts;
   if (rep) memset(rep, 0, sizeof(*rep));
   return solve_heat(t, m, ncomp, f_dev, g_dev, dtype, alpha_finest, o, rep, (cudaStream_t)cuda_stream);

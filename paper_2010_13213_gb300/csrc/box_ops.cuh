@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "box.cuh"
+#include "box_tc.cuh"
 #include "internal.h"
 
 namespace lgf {
@@ -48,16 +49,70 @@ struct BoxOps {
   // kernel, inverse (scattering through ore[f] / oim[f]).  A field whose input is real (one spec, real
   // part) and whose imaginary output is unused runs on the Hermitian half K1x <= Px/2.  Y0/Y1 hold
   // min(nf, BOX_MAXF) * P^3 B^3 complex R each.  `mark(phase)` is called after the forward, kernel and
-  // inverse stages of every group of fields (phase timing; may be null).
+  // inverse stages of every group of fields (phase timing; may be null).  `slices` > 0 runs the six
+  // block-index DFT passes as tensor-core GEMMs with that many BF16 digit slices (float: 1-3,
+  // double-float: 4-6); a bounded wait that gives up there sets *status.
   static int convolve(int B, const BoxSpec *S, int nf, const int *nin, const InSpec3 *in,
                       const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1,
-                      cudaStream_t st, void (*mark)(void *, int) = nullptr, void *mark_ctx = nullptr);
+                      cudaStream_t st, void (*mark)(void *, int) = nullptr, void *mark_ctx = nullptr,
+                      int slices = 0, int *status = nullptr);
 };
+
+// Launch of one tensor-core pass: persistent CTAs, residency capped so that the CTAs on an SM never
+// ask for more than its 512 TMEM columns (tcgen05.alloc would otherwise wait for a neighbour).
+template <class R, int B, int SL>
+static void tc_pass_launch(const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
+                           const TcMat &M, int inverse, int gather, int final, int nfield, int lines,
+                           const FwdSpecs &sp, const InvOuts<R> &outs, double sc, int *status, cudaStream_t st) {
+  static int nsm = 0;
+  static bool attr = false;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (!attr) {
+    cudaFuncSetAttribute(k_bdft_tc<R, B, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  const TcSmem pl = tc_smem_plan(SL, M.Kp, M.Np);
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(SL * M.Np)) cols <<= 1;
+  constexpr int SM_BYTES = 228 * 1024, CTA_RESERVED = 1024;
+  int cps = std::min<int>(4, 512 / (int)cols);
+  cps = std::min(cps, SM_BYTES / (pl.total + CTA_RESERVED));
+  const int req = std::max(pl.total, SM_BYTES / (cps + 1) - CTA_RESERVED + 16);
+  const int ntiles = nfield * lines * (B * B * B / TC_ROWS);
+  const int grid = std::min(ntiles, nsm * cps);
+  k_bdft_tc<R, B, SL><<<grid, TC_ROWS, req, st>>>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield,
+                                                  lines, sp, outs, sc, cols, pl, status);
+}
+
+template <class R, int B>
+static int tc_pass(int slices, const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
+                   const TcMat &M, int inverse, int gather, int final, int nfield, int lines, const FwdSpecs &sp,
+                   const InvOuts<R> &outs, double sc, int *status, cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value) {
+    switch (slices) {
+      case 1: tc_pass_launch<R, B, 1>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 2: tc_pass_launch<R, B, 2>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 3: tc_pass_launch<R, B, 3>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+    }
+  } else if constexpr (std::is_same<R, df>::value) {
+    switch (slices) {
+      case 4: tc_pass_launch<R, B, 4>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 5: tc_pass_launch<R, B, 5>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 6: tc_pass_launch<R, B, 6>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+    }
+  }
+  return set_error(LGF_E_INVALID_ARG, "%d DFT-GEMM slices are not available for this precision", slices);
+}
 
 template <class R, int B>
 static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real, const int *nin,
                      const InSpec3 *in, const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0,
-                     cx<R> *Y1, cudaStream_t st, void (*mark)(void *, int), void *mark_ctx) {
+                     cx<R> *Y1, cudaStream_t st, void (*mark)(void *, int), void *mark_ctx, int slices,
+                     int *status) {
   constexpr int B3 = B * B * B;
   BoxGeom g;
   for (int a = 0; a < 3; ++a) {
@@ -87,11 +142,23 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real
     outs.re[f] = ore[fi];
     outs.im[f] = oim[fi];
   }
+  int rc = LGF_OK;
   auto pass = [&](const cx<R> *in_, cx<R> *out_, int ax, int3 ext, int lines, int inverse, int gather, int final,
                   double sc) {
     const int nb_ax = nb[ax];
     const bool realx = ax == 0 && g.pxu < P[0];
     const int nout = inverse ? nb_ax : (realx ? g.pxu : 2 * nb_ax);
+    if (slices > 0) {
+      TcMat M = S->tcm[ax][inverse ? (realx ? 2 : 1) : 0];
+      if (realx && !inverse) {  // the first pxu outputs of the forward matrix
+        M.nout = g.pxu;
+        M.Np = (2 * g.pxu + 15) / 16 * 16;
+      }
+      const int r = tc_pass<R, B>(slices, in_, out_, fstride, g, ax, ext, M, inverse, gather, final, n, lines, sp,
+                                  outs, sc, status, st);
+      if (r && !rc) rc = r;
+      return;
+    }
     if (nout <= 8) {
       k_bdft<R, B, 8, 2><<<dim3((B3 + 511) / 512, lines, n), 256, 0, st>>>(
           in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), inverse, gather, final, 1, sp, outs, sc);
@@ -115,13 +182,13 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real
   pass(Y1, Y0, 1, make_int3(pxu, 0, nb[2]), pxu * nb[2], 1, 0, 0, 1.0);
   pass(Y0, Y1, 0, make_int3(0, nb[1], nb[2]), nb[1] * nb[2], 1, 0, 1, scale);
   if (mark) mark(mark_ctx, 4);
-  return LGF_OK;
+  return rc;
 }
 
 template <class R, int B>
 static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec3 *in, const OutSpec<R> *ore,
                           const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
-                          void (*mark)(void *, int), void *mark_ctx) {
+                          void (*mark)(void *, int), void *mark_ctx, int slices, int *status) {
   std::vector<int> cplx, real;
   for (int f = 0; f < nf; ++f) {
     const bool is_real = nin[f] == 1 && in[f].s[0].part == 0 && oim[f].scatter == nullptr;
@@ -131,7 +198,8 @@ static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec
     const std::vector<int> &lst = pass ? real : cplx;
     for (size_t f0 = 0; f0 < lst.size(); f0 += BOX_MAXF) {
       std::vector<int> grp(lst.begin() + f0, lst.begin() + std::min(lst.size(), f0 + BOX_MAXF));
-      int rc = box_group<R, B>(S, grp, pass == 1, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
+      int rc = box_group<R, B>(S, grp, pass == 1, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices,
+                               status);
       if (rc) return rc;
     }
   }
@@ -142,9 +210,13 @@ static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec
 template <class R>
 int BoxOps<R>::convolve(int B, const BoxSpec *S, int nf, const int *nin, const InSpec3 *in,
                         const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1,
-                        cudaStream_t st, void (*mark)(void *, int), void *mark_ctx) {
-  if (B == 8) return box_convolve_b<R, 8>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
-  if (B == 16) return box_convolve_b<R, 16>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx);
+                        cudaStream_t st, void (*mark)(void *, int), void *mark_ctx, int slices, int *status) {
+  if (slices > 0 && (std::is_same<R, double>::value || !status))
+    return set_error(LGF_E_UNSUPPORTED, "the tensor-core DFT-GEMM runs in FP32 or double-float only");
+  if (B == 8)
+    return box_convolve_b<R, 8>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status);
+  if (B == 16)
+    return box_convolve_b<R, 16>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status);
   return set_error(LGF_E_UNSUPPORTED, "block size %d", B);
 }
 

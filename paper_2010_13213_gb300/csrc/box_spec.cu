@@ -5,6 +5,7 @@
 // four-step order of box.cuh.  G is real and even so Ghat is real.  Computed once in FP64 (dense
 // block-index DFTs + the local FFT of k_box_mid), then rounded to FP32 and split into double-float.
 #include <math.h>
+#include <string.h>
 
 #include <vector>
 
@@ -47,7 +48,64 @@ void twiddles_host(int N, std::vector<double> &c, std::vector<double> &s) {
   }
 }
 
+// Coefficient digits of one block-index DFT pass (box_tc.cuh): C_jo = W_P^{-+jo} (dir -1 forward, +1
+// inverse); `realw`: the Hermitian-folded real inverse, weights 1 (j = 0, 2j = P) or 2 and real output
+// only.  M^T[n = 2o + p][k = 2j + q] / sigma = 2^{-7} sum_t c_t 2^{-8t} with integer digits |c_t| <= 128.
+static void tc_matrix(int P, int nin, int nout, int dir, bool realw, const std::vector<double> &c,
+                      const std::vector<double> &s, std::vector<uint16_t> &buf, TcMat &M) {
+  const int K = 2 * nin, N = 2 * nout;
+  M.nin = nin;
+  M.nout = nout;
+  M.Kp = (K + 15) / 16 * 16;
+  M.Np = (N + 15) / 16 * 16;
+  M.sigma = realw ? 2.0f : 1.0f;
+  M.plane16 = M.Np * M.Kp * 2 / 16;
+  const size_t off = buf.size(), plane = (size_t)M.Np * M.Kp;
+  buf.resize(off + TC_SMAX * plane, 0);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      const int j = k / 2, q = k % 2, o = n / 2, p = n % 2;
+      const int idx = (int)(((int64_t)j * o) % P);
+      const double w = realw ? ((j == 0 || 2 * j == P) ? 1.0 : 2.0) : 1.0;
+      const double cr = w * c[idx], ci = w * (dir < 0 ? -s[idx] : s[idx]);
+      double v;
+      if (p == 0) v = q == 0 ? cr : -ci;
+      else v = realw ? 0.0 : (q == 0 ? ci : cr);
+      double r = v / (double)M.sigma * 128.0;
+      const size_t pos = ((size_t)(n / 8) * (M.Kp / 8) + k / 8) * 64 + (n % 8) * 8 + (k % 8);
+      for (int t = 0; t < TC_SMAX; ++t) {
+        const double d = nearbyint(r);
+        r = (r - d) * 256.0;
+        const float fd = (float)d;  // |d| <= 128: exact in bf16 (the top half of the float)
+        uint32_t bits;
+        memcpy(&bits, &fd, 4);
+        buf[off + t * plane + pos] = (uint16_t)(bits >> 16);
+      }
+    }
+  M.d = reinterpret_cast<const uint16_t *>(off);  // offset for now; rebased after the upload
+}
+
+static int tc_matrices(BoxSpec *S, const BoxGeom &g, cudaStream_t st) {
+  std::vector<uint16_t> buf;
+  for (int a = 0; a < 3; ++a) {
+    std::vector<double> c, s;
+    twiddles_host(g.P[a], c, s);
+    tc_matrix(g.P[a], g.nb[a], g.P[a], -1, false, c, s, buf, S->tcm[a][0]);
+    tc_matrix(g.P[a], g.P[a], g.nb[a], +1, false, c, s, buf, S->tcm[a][1]);
+    if (a == 0) tc_matrix(g.P[a], g.P[a] / 2 + 1, g.nb[a], +1, true, c, s, buf, S->tcm[a][2]);
+  }
+  if (cudaMalloc(&S->tcw, buf.size() * 2) != cudaSuccess) return set_error(LGF_E_OOM, "tensor-core coefficients");
+  cudaMemcpyAsync(S->tcw, buf.data(), buf.size() * 2, cudaMemcpyHostToDevice, st);
+  for (int a = 0; a < 3; ++a)
+    for (int v = 0; v < 3; ++v)
+      if (S->tcm[a][v].Np) S->tcm[a][v].d = S->tcw + reinterpret_cast<size_t>(S->tcm[a][v].d);
+  S->bytes += buf.size() * 2;
+  cudaError_t e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "coefficient upload: %s", cudaGetErrorString(e));
+}
+
 BoxSpec::~BoxSpec() {
+  cudaFree(tcw);
   cudaFree(g64);
   cudaFree(g32);
   cudaFree(gdf);
@@ -137,7 +195,7 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
   wP[0] = wP[1] = wP[2] = nullptr;
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return set_error(LGF_E_CUDA, "box spectrum kernels failed: %s", cudaGetErrorString(e));
-  return LGF_OK;
+  return tc_matrices(S, g, st);
 }
 
 int box_spectrum(lgf_table *t, const int nb[3], BoxSpec **out, cudaStream_t st) {

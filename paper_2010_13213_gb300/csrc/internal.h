@@ -16,6 +16,7 @@
 namespace lgf {
 
 int set_error(int code, const char *fmt, ...);
+int check_slices(const lgf_solve_opts &o);
 
 // Twiddles W_64^j from long-double cos/sin of the first octant and exact symmetries.
 template <class R>
@@ -88,6 +89,19 @@ struct PairOps {
 };
 
 // Kernel spectrum and twiddles of the block-index FFT mode for one box shape (box_spec.cu).
+#define TC_SMAX 6  // most digit slices of the tensor-core DFT-GEMM
+
+// Digit planes of one block-index DFT pass's coefficient matrix for the tensor-core path (box_tc.cuh):
+// M^T with Np rows (real output columns 2o + re/im) and Kp columns (real inputs 2j + re/im), bf16 bit
+// patterns in 8 x 8 core-matrix order, TC_SMAX planes `plane16` 16-byte units apart.
+struct TcMat {
+  const uint16_t *d = nullptr;
+  int nin = 0, nout = 0;  // complex inputs and outputs of the pass
+  int Kp = 0, Np = 0;     // GEMM K and N, multiples of 16
+  float sigma = 1.0f;     // power-of-two scale of the coefficient digits
+  int plane16 = 0;
+};
+
 struct BoxSpec {
   int nb[3] = {0, 0, 0};
   double *g64 = nullptr;  // [P^3 blocks][B^3] real spectrum, FP64
@@ -99,6 +113,8 @@ struct BoxSpec {
   cx<double> bw64[3][32];  // W_P^n per axis, n < P (host copies for kernel parameters)
   cx<float> bw32[3][32];
   cx<df> bwdf[3][32];
+  uint16_t *tcw = nullptr;  // device storage of the tensor-core coefficient digits
+  TcMat tcm[3][3];          // per axis: forward, inverse, Hermitian-folded real inverse (axis 0 only)
   size_t bytes = 0;
   ~BoxSpec();
 };
@@ -140,6 +156,9 @@ struct Workspace {
 
 namespace lgf {
 int box_spectrum(lgf_table *t, const int nb[3], BoxSpec **out, cudaStream_t st);
+// Synchronous read of the table's device status word; LGF_E_TIMEOUT (and the word cleared) when a
+// bounded device-side wait gave up since the last read.
+int take_device_status(lgf_table *t);
 }
 
 struct lgf_table {
@@ -158,4 +177,5 @@ struct lgf_table {
   std::mutex mu;
   std::map<void *, lgf::Workspace *> ws;  // keyed by stream
   std::map<std::tuple<int, int, int>, lgf::BoxSpec *> box;  // block-index FFT spectra by box shape
+  int *d_status = nullptr;  // device status word: nonzero after a bounded device wait gave up
 };

@@ -163,7 +163,7 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
   for (int k = 0; k < K; ++k) {
     const LevelPlan &L = P->L[k];
     if (!L.box_ok || L.Tall.empty()) continue;
-    if (o.mac_mode == LGF_MAC_BOX || !Gh) {
+    if (o.mac_mode == LGF_MAC_BOX || !Gh || (o.mac_mode == LGF_MAC_AUTO && o.dft_slices > 0)) {
       use_box[k] = 1;
     } else if (o.mac_mode == LGF_MAC_AUTO) {
       const bool packAB = !L.Tpsi.empty() || !L.SB.empty();
@@ -283,7 +283,7 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       }
       const int nf = (int)nin.size();
       if ((rc = BoxOps<R>::convolve(B, S, nf, nin.data(), in.data(), ore.data(), oim.data(), scale, Y0, Y1, st,
-                                    o.timing ? phase_mark_cb : nullptr, &tm)))
+                                    o.timing ? phase_mark_cb : nullptr, &tm, o.dft_slices, t->d_status)))
         return rc;
       launches += 7 * ((nf + BOX_MAXF - 1) / BOX_MAXF);
       target_cells += L.n_omega;
@@ -379,12 +379,13 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     for (int k = 0; k < K; ++k)
       if (use_box[k]) rep->mac_mode_used = LGF_MAC_BOX;
   }
-  if (o.residual && o.residual_tol > 0 && resid > o.residual_tol)
-    return set_error(LGF_E_PRECISION, "FP64 residual %.3e exceeds the tolerance %.3e", resid, o.residual_tol);
-  if (o.timing) {
+  if (o.timing || o.residual) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(LGF_E_CUDA, "solve failed: %s", cudaGetErrorString(e));
+    if (o.dft_slices > 0 && (rc = take_device_status(t))) return rc;
   }
+  if (o.residual && o.residual_tol > 0 && resid > o.residual_tol)
+    return set_error(LGF_E_PRECISION, "FP64 residual %.3e exceeds the tolerance %.3e", resid, o.residual_tol);
   return LGF_OK;
 }
 

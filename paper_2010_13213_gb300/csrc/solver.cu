@@ -234,7 +234,7 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
   }
   if ((rc = BoxOps<R>::convolve(B, S, nf, nin.data(), in.data(), ore.data(), oim.data(), scale,
                                 (cx<R> *)ws->buf[0].p, (cx<R> *)ws->buf[1].p, st,
-                                o.timing ? phase_mark_cb : nullptr, &tm)))
+                                o.timing ? phase_mark_cb : nullptr, &tm, o.dft_slices, t->d_status)))
     return rc;
   const int64_t launches = 7 * ((nf + BOX_MAXF - 1) / BOX_MAXF);
   tm.finish(rep);
@@ -242,6 +242,7 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
   if (o.timing) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(LGF_E_CUDA, "solve failed: %s", cudaGetErrorString(e));
+    if (o.dft_slices > 0 && (rc = take_device_status(t))) return rc;
   }
   return LGF_OK;
 }
@@ -255,7 +256,8 @@ static int solve_single_any(lgf_table *t, const lgf_mesh *m, int ncomp, const vo
   if (P->ntgt == 0) return LGF_OK;
   int mode = o.mac_mode;
   if (mode == LGF_MAC_AUTO)
-    mode = (P->box_ok && (!spectra_of<R>(t) || box_cost(m->block, P->nb) < pair_cost(m->block, P->nsrc, P->ntgt)))
+    mode = (P->box_ok && (!spectra_of<R>(t) || o.dft_slices > 0 ||
+                          box_cost(m->block, P->nb) < pair_cost(m->block, P->nsrc, P->ntgt)))
                ? LGF_MAC_BOX
                : LGF_MAC_PAIR;
   if (mode == LGF_MAC_BOX) {

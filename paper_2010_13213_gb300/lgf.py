@@ -46,7 +46,7 @@ class lgf_mesh(ctypes.Structure):
 
 class lgf_solve_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("mac_mode", c_int32), ("residual", c_int32),
-                ("timing", c_int32), ("residual_tol", c_double)]
+                ("timing", c_int32), ("residual_tol", c_double), ("dft_slices", c_int32), ("reserved", c_int32)]
 
 
 class lgf_report(ctypes.Structure):
@@ -89,11 +89,13 @@ def load():
         lib.lgf_batch_graph_create.argtypes = [c_void_p, c_int32, PP, PP, PP, PP, c_void_p]
         lib.lgf_batch_graph_launch.argtypes = [c_void_p, c_void_p]
         lib.lgf_batch_graph_nodes.argtypes = [c_void_p, POINTER(c_int64)]
+        lib.lgf_device_status.argtypes = [c_void_p]
         lib.lgf_last_error.restype = c_char_p
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
                      "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_batch_create", "lgf_batch_destroy",
-                     "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes"):
+                     "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
+                     "lgf_device_status"):
             getattr(lib, name).restype = c_int32
         _LIB = lib
     return _LIB
@@ -149,8 +151,14 @@ def lgf_table_lgf_values(table, n: int) -> np.ndarray:
     return out.reshape(n + 1, n + 1, n + 1)
 
 
-def _opts(precision=LGF_PREC_FP64, mac_mode=LGF_MAC_AUTO, residual=0, timing=0, residual_tol=0.0):
-    return lgf_solve_opts(int(precision), int(mac_mode), int(residual), int(timing), float(residual_tol))
+def _opts(precision=LGF_PREC_FP64, mac_mode=LGF_MAC_AUTO, residual=0, timing=0, residual_tol=0.0, dft_slices=0):
+    return lgf_solve_opts(int(precision), int(mac_mode), int(residual), int(timing), float(residual_tol),
+                          int(dft_slices), 0)
+
+
+def lgf_device_status(table) -> None:
+    """Synchronise and raise LgfError(LGF_E_TIMEOUT) if a bounded device wait gave up since the last read."""
+    _check(load().lgf_device_status(c_void_p(table)))
 
 
 def lgf_poisson_solve(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, dtype: int = LGF_F64,
