@@ -106,40 +106,53 @@ def _phases(ph):
     return {n: float(v) for n, v in zip(PHASE_NAMES, ph) if v}
 
 
-CMAC, CADD, CNORM, CMUL, DFMUL = 48, 16, 6, 38, 7  # FP32 instructions of the double-float ops (common.cuh)
+CADD, CNORM, CMUL, DFMUL, RFMA, DOT2, DFADD = 16, 6, 38, 7, 12, 24, 14  # FP32 instructions of the
+# double-float operations (common.cuh): lazy complex add, renormalisation of a complex value, complex
+# product, product by a real power-of-two-free constant, real multiply-add, real two-term dot product
+# with accumulation, renormalised real add (+ renormalisation)
 
 
-def _dft_pass_inst(P, nin, nout, lines, B3, double_first=False):
-    """One block-index DFT pass: every (input j, output k) pair is a multiply-add unless W^{jk} = 1."""
-    per = sum((CADD if (j * k) % P == 0 else CMAC) for j in range(nin) for k in range(nout)) + nout * CNORM
-    if double_first:  # real-field inverse x pass doubles the interior inputs (one lazy add each)
-        per += max(nin - 2, 0) * CADD
+def _fwd_pass_inst(nb, lines, B3, both):
+    """Conjugate-pair forward block-index DFT of nb inputs to P = 2 nb outputs (k_bdft_fwd): slots q = 0
+    and q = nb take sums, the nb - 1 pairs accumulate A, B with real coefficients; `both`: store X_k and
+    X_{P-k} (False: the Hermitian half of a real field)."""
+    per = (nb + 1) * CADD + (nb - 1) * (2 * CADD + (nb - 1) * 4 * RFMA)
+    per += 2 * CNORM + (nb - 1) * (2 if both else 1) * 2 * DFADD
+    return lines * B3 * per
+
+
+def _inv_pass_inst(nb, lines, B3, real):
+    """Conjugate-pair inverse of P = 2 nb inputs to nb outputs (k_bdft_inv): per input pair U, V (two
+    complex adds) then a two-term real dot product per output part (one part for a real field)."""
+    per = 2 * nb * CADD + (nb - 1) * (2 * CADD + CADD + (nb - 1) * (1 if real else 2) * DOT2) + nb * CNORM
     return lines * B3 * per
 
 
 def df_box_instructions(B, nb, ncomp):
     """FP32 instructions the double-float block-index FFT mode executes per solve, counted from the
-    arithmetic of the kernels (not measured): block-index DFT passes (k_bdft) and the fused local-FFT
-    kernel (k_box_mid).  Components ride two per complex field; an odd last component is a real field
-    kept on the Hermitian half K1x <= Px/2."""
+    arithmetic of the kernels (not measured): the six block-index DFT passes (k_bdft_fwd / k_bdft_inv)
+    and the fused local-FFT kernel (k_box_mid).  Components ride two per complex field; an odd last
+    component is a real field kept on the Hermitian half K1x <= Px/2."""
     import math
     nx, ny, nz = nb
     px, py, pz = 2 * nx, 2 * ny, 2 * nz
     B3 = B ** 3
     lg = int(math.log2(B))
-    twiddled = sum((B // ln) * (ln // 2 - 1) for ln in [2 ** s for s in range(1, lg + 1)])
+    # radix-2 FFT of B points: twiddled butterflies except W = 1 and W = -i (an exact swap)
+    twiddled = sum(sum(1 for j in range(1, ln // 2) if j * (64 // ln) != 16) * (B // ln)
+                   for ln in [2 ** s for s in range(1, lg + 1)])
     fft1d = twiddled * CMUL + (B // 2) * lg * 2 * CADD + B * CNORM
     mid_block = 6 * B * B * fft1d + 2 * B3 * 2 * CMUL + B3 * 2 * DFMUL
     dft = mid = 0
     fields = [px] * (ncomp // 2) + [px // 2 + 1] * (ncomp % 2)
     for pxu in fields:
         real = pxu < px
-        dft += _dft_pass_inst(px, nx, pxu, ny * nz, B3)                    # forward x
-        dft += _dft_pass_inst(py, ny, py, pxu * nz, B3)                    # forward y
-        dft += _dft_pass_inst(pz, nz, pz, pxu * py, B3)                    # forward z
-        dft += _dft_pass_inst(pz, pz, nz, pxu * py, B3)                    # inverse z
-        dft += _dft_pass_inst(py, py, ny, pxu * nz, B3)                    # inverse y
-        dft += _dft_pass_inst(px, pxu, nx, ny * nz, B3, double_first=real)  # inverse x
+        dft += _fwd_pass_inst(nx, ny * nz, B3, not real)      # forward x
+        dft += _fwd_pass_inst(ny, pxu * nz, B3, True)         # forward y
+        dft += _fwd_pass_inst(nz, pxu * py, B3, True)         # forward z
+        dft += _inv_pass_inst(nz, pxu * py, B3, False)        # inverse z
+        dft += _inv_pass_inst(ny, pxu * nz, B3, False)        # inverse y
+        dft += _inv_pass_inst(nx, ny * nz, B3, real)          # inverse x
         mid += pxu * py * pz * mid_block
     return dft, mid
 
@@ -159,7 +172,7 @@ def roofline_entry(case, B, ncomp, rep, ph):
         if ph[3] >= ph[2] + ph[4]:
             inst, ms, kern, launches = local, ph[3], "k_box_mid<df,16> (twiddle + local FFT + kernel + inverse)", ngroups
         else:
-            inst, ms, kern, launches = dft, ph[2] + ph[4], "k_bdft<df,16> (block-index DFT passes)", 6 * ngroups
+            inst, ms, kern, launches = dft, ph[2] + ph[4], "k_bdft_fwd/inv<df,16> (block-index DFT passes)", 6 * ngroups
     ach = inst / (ms * 1e-3)
     return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": FP32_INST_PEAK / 1e12,
             "unit": "T FP32-inst/s", "frac": ach / FP32_INST_PEAK, "traffic": None,

@@ -86,71 +86,64 @@ LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
 }
 
 // ------------------------------------------------------------------ block-index DFTs
-// Pass along axis `ax`: for every line (the two other block coordinates within `ext`) and every local
-// cell m:
-//   forward  out[.. k ..][m] = sum_{j < nb}  W_P^{ j k} in[.. j ..][m],   k < P = 2 nb
-//   inverse  out[.. j ..][m] = sum_{k < P}   W_P^{-j k} in[.. k ..][m],   j < nb (unnormalised)
-// A thread owns CELLS cells (m, m + 256, ...) and a chunk of at most CH consecutive outputs;
-// grid = (B^3 / (256 CELLS), lines, field * nchunk + chunk).  The first forward pass (gather) reads
+// Pass along axis `ax` for every line (the two other block coordinates within `ext`) and local cell m:
+//   forward  X[.. k ..][m] = sum_{j < nb} W_P^{ j k} x[.. j ..][m],   k < P = 2 nb
+//   inverse  y[.. j ..][m] = sum_{k < P}  W_P^{-j k} X[.. k ..][m],   j < nb (unnormalised)
+// Both use the conjugate symmetry W_P^{j(P-k)} = conj(W_P^{jk}) (c = cos(2 pi jk/P), s = sin(2 pi jk/P)):
+//   forward  A_k = sum_j c x_j, B_k = sum_j s x_j, X_k = A_k - i B_k, X_{P-k} = A_k + i B_k (1 <= k < P/2),
+//   inverse  y_j += c (X_k + X_{P-k}) + i s (X_k - X_{P-k}) per input pair,
+// so every multiply has a real coefficient: half the work of the complex products.  k = 0 and k = P/2
+// (coefficients 1 and (-1)^j) are sums.  A real field keeps K1x in [0, P/2] (Hermitian half): its
+// forward x pass stores X_k only and its inverse x pass takes X_{P-k} = conj(X_k) (real output).
+// A thread owns CELLS cells (m, m + NT, ...) and a chunk of CH pair slots (forward) or outputs (inverse);
+// grid = (B^3 / (NT CELLS), lines, field * nchunk + chunk).  The chunk's (c, s) sit in a shared table;
+// the next input is fetched while the current one multiplies.  The first forward pass (gather) reads
 // through the field's input specs, the last inverse pass (final) writes through its output specs.
 // Field f's arrays start at in + f * fstride, out + f * fstride.
-template <class R, int B, int CH, int CELLS>
-__global__ void __launch_bounds__(256) k_bdft(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
-                                              int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
-                                              int inverse, int gather, int final, int nchunk, FwdSpecs sp,
-                                              InvOuts<R> outs, double scale) {
+template <class R, int B, int CH, int CELLS, int NT>
+__global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
+                                                 int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
+                                                 int gather, int nchunk, FwdSpecs sp) {
   constexpr int B3 = B * B * B;
-  const int nb = g.nb[ax];
-  const int P = 2 * nb;
+  __shared__ R Tc[BOX_NB_MAX][CH], Ts[BOX_NB_MAX][CH];
+  const int nb = g.nb[ax], P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
-  const int line = blockIdx.y;
-  const int l1 = line % e1, l2 = line / e1;
+  const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
   const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
-  // a real field keeps K1x in [0, Px/2] only: the forward x pass stops there and the inverse x pass
-  // folds the missing half in as the conjugate (weights 1, 2, ..., 2, 1 on the real part)
   const bool realx = ax == 0 && g.pxu < P;
-  const int nout = inverse ? nb : (realx ? g.pxu : P), nin = inverse ? (realx ? g.pxu : P) : nb;
-  const int o0 = chunk * CH;
-  const int no = nout - o0 < CH ? nout - o0 : CH;
-  const int m0 = blockIdx.x * (256 * CELLS) + threadIdx.x;
-  const int64_t bsa = g.bs[ax] * (int64_t)B3;  // element stride along the pass axis
+  const int q0 = chunk * CH;
+  const int nq = min(CH, half + 1 - q0);  // pair slots q = 0 .. P/2
+  for (int i = threadIdx.x; i < nb * CH; i += NT) {
+    const int j = i / CH, c = i % CH;
+    const int n = (int)(((int64_t)j * (q0 + c)) % P);
+    Tc[j][c] = tw.w[n].re;
+    Ts[j][c] = -tw.w[n].im;
+  }
+  const int m0 = blockIdx.x * (NT * CELLS) + threadIdx.x;
+  const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
-  // gather / scatter block indices: box block (x, y, z) -> (z * nby + y) * nbx + x
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
-  const int gs1 = a1 == 0 ? 1 : g.nb[0];
-  const int gs2 = a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1];
-  const int gbase = l1 * gs1 + l2 * gs2;
+  const int gbase = l1 * (a1 == 0 ? 1 : g.nb[0]) + l2 * (a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   InSpec s0{}, s1{}, s2{};
   int ns = 0;
-  OutSpec<R> ore{}, oim{};
+  if (gather) {
 #pragma unroll
-  for (int f = 0; f < BOX_MAXF; ++f)
-    if (f == field) {
-      if (gather) {
+    for (int f = 0; f < BOX_MAXF; ++f)
+      if (f == field) {
         s0 = sp.s[f][0];
         s1 = sp.s[f][1];
         s2 = sp.s[f][2];
         ns = sp.n[f];
       }
-      if (final) {
-        ore = outs.re[f];
-        oim = outs.im[f];
-      }
-    }
+  }
   const cx<R> *src = in + field * fstride + lbase;
-  cx<R> acc[CELLS][CH];
-#pragma unroll
-  for (int c = 0; c < CELLS; ++c)
-#pragma unroll
-    for (int k = 0; k < CH; ++k) acc[c][k] = cx_zero<R>();
-  for (int j = 0; j < nin; ++j) {
-    cx<R> x[CELLS];
+  auto fetch = [&](int j, cx<R>(&x)[CELLS]) {
     if (gather) {
       const int bidx = gbase + j * gsa;
 #pragma unroll
       for (int c = 0; c < CELLS; ++c) {
-        const int m = m0 + 256 * c;
+        const int m = m0 + NT * c;
         R re = RT<R>::zero(), im = RT<R>::zero();
         auto add = [&](const InSpec &q) {
           const int idx = q.gather[bidx];
@@ -168,42 +161,170 @@ __global__ void __launch_bounds__(256) k_bdft(const cx<R> *__restrict__ in, cx<R
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < CELLS; ++c) x[c] = src[j * bsa + m0 + 256 * c];
+      for (int c = 0; c < CELLS; ++c) x[c] = src[j * bsa + m0 + NT * c];
     }
-    if (realx && inverse && j != 0 && 2 * j != P)
+  };
+  __syncthreads();
+  cx<R> A[CELLS][CH], Bv[CELLS][CH];
 #pragma unroll
-      for (int c = 0; c < CELLS; ++c) x[c] = cx<R>{x[c].re + x[c].re, x[c].im + x[c].im};
-    int n = (int)(((int64_t)j * o0) % P);  // (j * k) mod P for k = o0, o0 + 1, ...
+  for (int c = 0; c < CELLS; ++c)
+#pragma unroll
+    for (int k = 0; k < CH; ++k) A[c][k] = Bv[c][k] = cx_zero<R>();
+  cx<R> xn[CELLS];
+  fetch(0, xn);
+  for (int j = 0; j < nb; ++j) {
+    cx<R> x[CELLS];
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) x[c] = xn[c];
+    if (j + 1 < nb) fetch(j + 1, xn);
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
-      if (k < no) {
-        const cx<R> w = inverse ? conj(tw.w[n]) : tw.w[n];
+      if (k >= nq) break;
+      const int q = q0 + k;
+      if (j == 0 || q == 0) {
 #pragma unroll
-        for (int c = 0; c < CELLS; ++c) acc[c][k] = n ? cmac_lazy(acc[c][k], x[c], w) : cadd(acc[c][k], x[c]);
+        for (int c = 0; c < CELLS; ++c) A[c][k] = cadd(A[c][k], x[c]);
+      } else if (q == half) {
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) A[c][k] = (j & 1) ? csub(A[c][k], x[c]) : cadd(A[c][k], x[c]);
+      } else {
+        const R cc = Tc[j][k], ss = Ts[j][k];
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) {
+          A[c][k] = cx<R>{rfma(A[c][k].re, cc, x[c].re), rfma(A[c][k].im, cc, x[c].im)};
+          Bv[c][k] = cx<R>{rfma(Bv[c][k].re, ss, x[c].re), rfma(Bv[c][k].im, ss, x[c].im)};
+        }
       }
-      n += j;
-      if (n >= P) n -= P;
+    }
+  }
+  cx<R> *dst = out + field * fstride + lbase;
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    if (k >= nq) break;
+    const int q = q0 + k;
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+      const int m = m0 + NT * c;
+      if (q == 0 || q == half) {
+        dst[q * bsa + m] = cnorm(A[c][k]);
+      } else {
+        const cx<R> a = A[c][k], b = Bv[c][k];
+        dst[q * bsa + m] = cx<R>{rnorm(a.re + b.im), rnorm(a.im - b.re)};
+        if (!realx) dst[(P - q) * bsa + m] = cx<R>{rnorm(a.re - b.im), rnorm(a.im + b.re)};
+      }
+    }
+  }
+}
+
+template <class R, int B, int CH, int CELLS, int NT>
+__global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
+                                                 int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
+                                                 int final, int nchunk, InvOuts<R> outs, double scale) {
+  constexpr int B3 = B * B * B;
+  __shared__ R Tc[BOX_NB_MAX + 1][CH], Ts[BOX_NB_MAX + 1][CH];
+  const int nb = g.nb[ax], P = 2 * nb, half = nb;
+  const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
+  const int e1 = ax == 0 ? ext.y : ext.x;
+  const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
+  const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
+  const bool realx = ax == 0 && g.pxu < P;
+  const int o0 = chunk * CH;
+  const int no = min(CH, nb - o0);
+  for (int i = threadIdx.x; i < (half + 1) * CH; i += NT) {
+    const int q = i / CH, c = i % CH;
+    const int n = (int)(((int64_t)q * (o0 + c)) % P);
+    Tc[q][c] = tw.w[n].re;
+    Ts[q][c] = -tw.w[n].im;
+  }
+  const int m0 = blockIdx.x * (NT * CELLS) + threadIdx.x;
+  const int64_t bsa = g.bs[ax] * (int64_t)B3;
+  const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
+  const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
+  const int gbase = l1 * (a1 == 0 ? 1 : g.nb[0]) + l2 * (a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
+  const cx<R> *src = in + field * fstride + lbase;
+  // input slot q: X_q and (1 <= q < P/2) X_{P-q}, the latter conj(X_q) for a real field
+  auto fetch = [&](int q, cx<R>(&xa)[CELLS], cx<R>(&xb)[CELLS]) {
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+      xa[c] = src[q * bsa + m0 + NT * c];
+      if (q != 0 && q != half) xb[c] = realx ? conj(xa[c]) : src[(P - q) * bsa + m0 + NT * c];
+    }
+  };
+  __syncthreads();
+  cx<R> y[CELLS][CH];
+#pragma unroll
+  for (int c = 0; c < CELLS; ++c)
+#pragma unroll
+    for (int k = 0; k < CH; ++k) y[c][k] = cx_zero<R>();
+  cx<R> na[CELLS], nbv[CELLS];
+  fetch(0, na, nbv);
+  for (int q = 0; q <= half; ++q) {
+    cx<R> xa[CELLS], xb[CELLS];
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+      xa[c] = na[c];
+      xb[c] = nbv[c];
+    }
+    if (q < half) fetch(q + 1, na, nbv);
+    if (q == 0 || q == half) {
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        if (k >= no) break;
+        const bool neg = q == half && ((o0 + k) & 1);
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) y[c][k] = neg ? csub(y[c][k], xa[c]) : cadd(y[c][k], xa[c]);
+      }
+      continue;
+    }
+    cx<R> U[CELLS], V[CELLS];
+#pragma unroll
+    for (int c = 0; c < CELLS; ++c) {
+      U[c] = cadd(xa[c], xb[c]);
+      V[c] = csub(xa[c], xb[c]);
+    }
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      if (k >= no) break;
+      if (o0 + k == 0) {
+#pragma unroll
+        for (int c = 0; c < CELLS; ++c) y[c][k] = cadd(y[c][k], U[c]);
+        continue;
+      }
+      const R cc = Tc[q][k], ss = Ts[q][k];
+#pragma unroll
+      for (int c = 0; c < CELLS; ++c) {
+        y[c][k].re = rdot2(y[c][k].re, cc, U[c].re, ss, V[c].im, -1.0f);
+        if (!realx) y[c][k].im = rdot2(y[c][k].im, cc, U[c].im, ss, V[c].re, 1.0f);
+      }
     }
   }
   if (!final) {
     cx<R> *dst = out + field * fstride + lbase;
 #pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k < no)
+    for (int k = 0; k < CH; ++k) {
+      if (k >= no) break;
 #pragma unroll
-        for (int c = 0; c < CELLS; ++c) dst[(o0 + k) * bsa + m0 + 256 * c] = cnorm(acc[c][k]);
+      for (int c = 0; c < CELLS; ++c) dst[(o0 + k) * bsa + m0 + NT * c] = cnorm(y[c][k]);
+    }
     return;
   }
+  OutSpec<R> ore{}, oim{};
+#pragma unroll
+  for (int f = 0; f < BOX_MAXF; ++f)
+    if (f == field) {
+      ore = outs.re[f];
+      oim = outs.im[f];
+    }
   const R sc = RT<R>::from(scale);
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
-    if (k >= no) continue;
+    if (k >= no) break;
     const int bidx = gbase + (o0 + k) * gsa;
 #pragma unroll
     for (int c = 0; c < CELLS; ++c) {
-      const cx<R> v = cnorm(acc[c][k]);
-      box_store<R>(ore, bidx, m0 + 256 * c, B3, v.re * sc);
-      if (!realx) box_store<R>(oim, bidx, m0 + 256 * c, B3, v.im * sc);
+      const cx<R> v = cnorm(y[c][k]);
+      box_store<R>(ore, bidx, m0 + NT * c, B3, v.re * sc);
+      if (!realx) box_store<R>(oim, bidx, m0 + NT * c, B3, v.im * sc);
     }
   }
 }

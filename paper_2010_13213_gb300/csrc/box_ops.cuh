@@ -58,12 +58,13 @@ struct BoxOps {
                       int slices = 0, int *status = nullptr);
 };
 
-// Launch of one tensor-core pass: persistent CTAs, residency capped so that the CTAs on an SM never
-// ask for more than its 512 TMEM columns (tcgen05.alloc would otherwise wait for a neighbour).
+// Launch of one tensor-core pass: persistent CTAs of 128 threads, as many per SM as registers, shared
+// memory and the SM's 512 TMEM columns allow (shared memory is padded when TMEM is the limit, so that no
+// tcgen05.alloc has to wait for a neighbour).
 template <class R, int B, int SL>
 static void tc_pass_launch(const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
-                           const TcMat &M, int inverse, int gather, int final, int nfield, int lines,
-                           const FwdSpecs &sp, const InvOuts<R> &outs, double sc, int *status, cudaStream_t st) {
+                           const TcMat &M, int gather, int final, int nfield, int lines, const FwdSpecs &sp,
+                           const InvOuts<R> &outs, double sc, int *status, cudaStream_t st) {
   static int nsm = 0;
   static bool attr = false;
   if (!nsm) {
@@ -78,31 +79,42 @@ static void tc_pass_launch(const cx<R> *in, cx<R> *out, int64_t fstride, const B
   const TcSmem pl = tc_smem_plan(SL, M.Kp, M.Np);
   uint32_t cols = 32;
   while (cols < (uint32_t)(SL * M.Np)) cols <<= 1;
-  constexpr int SM_BYTES = 228 * 1024, CTA_RESERVED = 1024;
-  int cps = std::min<int>(4, 512 / (int)cols);
-  cps = std::min(cps, SM_BYTES / (pl.total + CTA_RESERVED));
-  const int req = std::max(pl.total, SM_BYTES / (cps + 1) - CTA_RESERVED + 16);
+  const int cap = 512 / (int)cols;
+  // residency from registers and shared memory; pad shared memory when TMEM would be over-subscribed
+  static int regs = 0;
+  if (!regs) {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_bdft_tc<R, B, SL>);
+    regs = std::max(fa.numRegs, 1);
+  }
+  constexpr int SM_BYTES = 228 * 1024, CTA_RESERVED = 1024, SM_REGS = 65536;
+  int req = pl.total;
+  int fit = std::min(SM_REGS / (((regs + 7) / 8 * 8) * TC_ROWS), SM_BYTES / (req + CTA_RESERVED));
+  if (fit > cap) {
+    req = std::max(req, SM_BYTES / (cap + 1) - CTA_RESERVED + 16);
+    fit = cap;
+  }
   const int ntiles = nfield * lines * (B * B * B / TC_ROWS);
-  const int grid = std::min(ntiles, nsm * cps);
-  k_bdft_tc<R, B, SL><<<grid, TC_ROWS, req, st>>>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield,
-                                                  lines, sp, outs, sc, cols, pl, status);
+  const int grid = std::min(ntiles, nsm * std::max(fit, 1));
+  k_bdft_tc<R, B, SL><<<grid, TC_ROWS, req, st>>>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines,
+                                                  sp, outs, sc, cols, pl, status);
 }
 
 template <class R, int B>
 static int tc_pass(int slices, const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
-                   const TcMat &M, int inverse, int gather, int final, int nfield, int lines, const FwdSpecs &sp,
+                   const TcMat &M, int gather, int final, int nfield, int lines, const FwdSpecs &sp,
                    const InvOuts<R> &outs, double sc, int *status, cudaStream_t st) {
   if constexpr (std::is_same<R, float>::value) {
     switch (slices) {
-      case 1: tc_pass_launch<R, B, 1>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
-      case 2: tc_pass_launch<R, B, 2>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
-      case 3: tc_pass_launch<R, B, 3>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 1: tc_pass_launch<R, B, 1>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 2: tc_pass_launch<R, B, 2>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 3: tc_pass_launch<R, B, 3>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
     }
   } else if constexpr (std::is_same<R, df>::value) {
     switch (slices) {
-      case 4: tc_pass_launch<R, B, 4>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
-      case 5: tc_pass_launch<R, B, 5>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
-      case 6: tc_pass_launch<R, B, 6>(in, out, fstride, g, ax, ext, M, inverse, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 4: tc_pass_launch<R, B, 4>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 5: tc_pass_launch<R, B, 5>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
+      case 6: tc_pass_launch<R, B, 6>(in, out, fstride, g, ax, ext, M, gather, final, nfield, lines, sp, outs, sc, status, st); return LGF_OK;
     }
   }
   return set_error(LGF_E_INVALID_ARG, "%d DFT-GEMM slices are not available for this precision", slices);
@@ -154,18 +166,29 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real
         M.nout = g.pxu;
         M.Np = (2 * g.pxu + 15) / 16 * 16;
       }
-      const int r = tc_pass<R, B>(slices, in_, out_, fstride, g, ax, ext, M, inverse, gather, final, n, lines, sp,
-                                  outs, sc, status, st);
+      const int r = tc_pass<R, B>(slices, in_, out_, fstride, g, ax, ext, M, gather, final, n, lines, sp, outs, sc,
+                                  status, st);
       if (r && !rc) rc = r;
       return;
     }
-    if (nout <= 8) {
-      k_bdft<R, B, 8, 2><<<dim3((B3 + 511) / 512, lines, n), 256, 0, st>>>(
-          in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), inverse, gather, final, 1, sp, outs, sc);
+    constexpr int NT = 128;
+    if (!inverse) {
+      const int slots = nb_ax + 1;  // conjugate pairs q = 0 .. P/2
+      if (slots <= 4) {
+        k_bdft_fwd<R, B, 4, 2, NT><<<dim3(B3 / (2 * NT), lines, n), NT, 0, st>>>(
+            in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, 1, sp);
+      } else {
+        const int nch = (slots + 3) / 4;
+        k_bdft_fwd<R, B, 4, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+            in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, nch, sp);
+      }
+    } else if (nout <= 8) {
+      k_bdft_inv<R, B, 8, 2, NT><<<dim3(B3 / (2 * NT), lines, n), NT, 0, st>>>(
+          in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, 1, outs, sc);
     } else {
       const int nch = (nout + 7) / 8;
-      k_bdft<R, B, 8, 1><<<dim3((B3 + 255) / 256, lines, n * nch), 256, 0, st>>>(
-          in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), inverse, gather, final, nch, sp, outs, sc);
+      k_bdft_inv<R, B, 8, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+          in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, nch, outs, sc);
     }
   };
   const int pxu = g.pxu;

@@ -70,8 +70,8 @@ LGF_D void tc_init(df &acc, float D) { acc = df{D, 0.0f}; }
 LGF_D float tc_scale(float a, float f) { return __fmul_rn(a, f); }
 LGF_D df tc_scale(df a, float f) { return df_scale2(a, f); }
 
-// Shared-memory plan of one launch (bytes): digit planes of X (S x 128 x Kp) then of M^T (S x Np x Kp),
-// then the mbarrier, the TMEM base address and the timeout flag.
+// Shared-memory plan of one launch (bytes): digit planes of X (S x 128 x Kp bf16), of M^T (S x Np x Kp),
+// then the mbarrier, the TMEM base address and the abort flag.
 struct TcSmem {
   int a_off, a_plane, b_off, b_plane, bar_off, total;
 };
@@ -88,36 +88,35 @@ inline TcSmem tc_smem_plan(int S, int Kp, int Np) {
 
 }  // namespace lgf
 
-// One pass.  grid: persistent CTAs over tiles (field, line, 128-cell chunk); 128 threads, thread = row.
-// `tmem_cols` (power of two >= S * Np) TMEM columns hold the S level accumulators of Np columns each.
-// A wait that runs out (about a second) sets *status = 1 and the CTA stops.
+// One pass.  Persistent CTAs of 128 threads (thread = row = cell of the tile) over tiles (field, line,
+// 128-cell chunk).  Per tile: load the rows and cut them into digits (shared memory); one thread issues
+// the S(S+1)/2 x Kp/16 MMAs (M = 128, N = Np, K = 16) into S level accumulators in TMEM and commits to
+// the mbarrier; all threads wait, read the levels back, recombine and store.  Several CTAs share an SM
+// (their phases overlap); each holds `tmem_cols` >= S Np columns.
+// A wait that runs out (about a second) sets *status = 1 and the CTA drains, frees its TMEM and stops.
 template <class R, int B, int S>
 __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                      int64_t fstride, BoxGeom g, int ax, int3 ext, lgf::TcMat M,
-                                                     int inverse, int gather, int final, int nfield, int lines,
-                                                     FwdSpecs sp, InvOuts<R> outs, double scale,
-                                                     uint32_t tmem_cols, lgf::TcSmem pl, int *status) {
+                                                     int gather, int final, int nfield, int lines, FwdSpecs sp,
+                                                     InvOuts<R> outs, double scale, uint32_t tmem_cols,
+                                                     lgf::TcSmem pl, int *status) {
   using namespace lgf;
   constexpr int B3 = B * B * B;
   constexpr int NCH = B3 / TC_ROWS;
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + pl.bar_off);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + pl.bar_off + 8);
-  int *abort_flag = reinterpret_cast<int *>(smem + pl.bar_off + 12);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + pl.bar_off + 12);
   const int row = threadIdx.x, warp = threadIdx.x >> 5;
   const int nin = M.nin, nout = M.nout, Kp = M.Kp, Np = M.Np;
   const int kg = Kp / 8;  // 16-byte K groups per row
-  const uint32_t sbo_a = (uint32_t)kg * 128u;
+  const uint32_t sbo = (uint32_t)kg * 128u;
 
-  // coefficient digit planes: identical for every tile, copied once
-  {
+  {  // coefficient digit planes: the same for every tile
     const uint4 *src = reinterpret_cast<const uint4 *>(M.d);
     uint4 *dst = reinterpret_cast<uint4 *>(smem + pl.b_off);
-    const int n16 = S * pl.b_plane / 16;
-    for (int i = threadIdx.x; i < n16; i += blockDim.x) {
-      const int p = i / (pl.b_plane / 16), q = i % (pl.b_plane / 16);
-      dst[i] = src[(int64_t)p * M.plane16 + q];
-    }
+    const int per = pl.b_plane / 16;
+    for (int i = threadIdx.x; i < S * per; i += blockDim.x) dst[i] = src[(int64_t)(i / per) * M.plane16 + i % per];
   }
   if (threadIdx.x == 0) {
     tc::mbar_init(bar, 1);
@@ -129,9 +128,9 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
+  const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
   uint32_t phase = 0;
 
-  const int nb = g.nb[ax];
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
@@ -142,12 +141,10 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
   const int ntiles = nfield * lines * NCH;
   const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, Np);
   const uint32_t a_base = tc::smem_addr(smem + pl.a_off), b_base = tc::smem_addr(smem + pl.b_off);
-  (void)nb;
+  const R sc = RT<R>::from(scale);
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int chunk = tile % NCH;
-    const int line = (tile / NCH) % lines;
-    const int field = tile / (NCH * lines);
+  for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+    const int chunk = tile % NCH, line = (tile / NCH) % lines, field = tile / (NCH * lines);
     const int l1 = line % e1, l2 = line / e1;
     const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
     const int gbase = l1 * gs1 + l2 * gs2;
@@ -188,30 +185,18 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
       if (ns > 2) add(s2);
       return cx<R>{re, im};
     };
-    // row scale: max |x| < 2^e
-    float mx = 0.0f;
-    for (int j = 0; j < nin; ++j) {
-      const cx<R> x = load(j);
-      mx = fmaxf(mx, fmaxf(tc_absmax(x.re), tc_absmax(x.im)));
-    }
-    // e is clamped at -100 so that 2^{7-e} stays finite for rows of denormal size (their digits are
-    // then those of a looser scale: absolute error below 2^-(100+7+8(S-1)))
+    // ---- digits of the row.  Row scale max |x| < 2^e; e >= -100 keeps 2^{7-e} finite for rows of
+    // denormal size (their digits then follow a looser scale: absolute error below 2^-(100+7+8(S-1))).
+    unsigned char *arow = smem + pl.a_off + (row >> 3) * sbo + (row & 7) * 16;
     int e = 0;
-    if (mx > 0.0f) frexpf(mx, &e);
-    e = max(e, -100);
-    const float sdown = ldexpf(1.0f, 7 - e);
-    // digits of the row, 4 complex inputs (one 16-byte K group) at a time
-    unsigned char *arow = smem + pl.a_off + (row >> 3) * sbo_a + (row & 7) * 16;
-    for (int grp = 0; grp < kg; ++grp) {
+    auto put_group = [&](int grp, const cx<R> (&x)[4], int nq, float sdown) {
       uint32_t w[S][4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int j = grp * 4 + q;
         float dr[S], di[S];
-        if (j < nin) {
-          const cx<R> x = load(j);
-          tc_digits<S>(x.re, sdown, dr);
-          tc_digits<S>(x.im, sdown, di);
+        if (q < nq) {
+          tc_digits<S>(x[q].re, sdown, dr);
+          tc_digits<S>(x[q].im, sdown, di);
         } else {
 #pragma unroll
           for (int t = 0; t < S; ++t) dr[t] = di[t] = 0.0f;
@@ -222,72 +207,90 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
 #pragma unroll
       for (int t = 0; t < S; ++t)
         *reinterpret_cast<uint4 *>(arow + t * pl.a_plane + grp * 128) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+    };
+    {
+      // two passes over groups of four inputs (max, then digits; the second mostly hits L1), the four
+      // loads of a group issued back to back
+      float mx = 0.0f;
+      for (int j0 = 0; j0 < nin; j0 += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j0 + q < nin) {
+            const cx<R> v = load(j0 + q);
+            mx = fmaxf(mx, fmaxf(tc_absmax(v.re), tc_absmax(v.im)));
+          }
+      }
+      if (mx > 0.0f) frexpf(mx, &e);
+      e = max(e, -100);
+      const float sdown = ldexpf(1.0f, 7 - e);
+#pragma unroll 1
+      for (int grp = 0; grp < kg; ++grp) {
+        cx<R> xs[4];
+        const int nq = min(4, max(0, nin - 4 * grp));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xs[q] = q < nq ? load(4 * grp + q) : cx_zero<R>();
+        put_group(grp, xs, nq, sdown);
+      }
     }
+    const float fsc = ldexpf(M.sigma, e - 14);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
+    // ---- MMAs of all S levels over the Np output columns, then recombination 16 columns at a time
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
-      const uint32_t sbo_b = sbo_a;  // M^T planes have the same K extent
-#pragma unroll 1
       for (int l = 0; l < S; ++l) {
-        const uint32_t dcol = tbase + (uint32_t)(l * Np);
-        int first = 1;
+        uint32_t acc = 0;
         for (int t = 0; t <= l; ++t) {
-          const int u = l - t;
-          for (int ks = 0; ks < Kp / 16; ++ks) {
-            const uint64_t ad = tc::smem_desc(a_base + t * pl.a_plane + ks * 256, 128, sbo_a);
-            const uint64_t bd = tc::smem_desc(b_base + u * pl.b_plane + ks * 256, 128, sbo_b);
-            tc::mma_bf16(dcol, ad, bd, idesc, first ? 0u : 1u);
-            first = 0;
+          const uint32_t ab = a_base + t * pl.a_plane, bb = b_base + (l - t) * pl.b_plane;
+          for (int ks = 0; ks < kg / 2; ++ks) {
+            tc::mma_bf16(tbase + (uint32_t)(l * Np), tc::smem_desc(ab + ks * 256, 128, sbo),
+                         tc::smem_desc(bb + ks * 256, 128, sbo), idesc, acc);
+            acc = 1;
           }
         }
       }
       tc::mma_commit(bar);
     }
-    if (!tc::mbar_wait_bounded(bar, phase)) *abort_flag = 1;
-    __syncthreads();
-    if (*abort_flag) {
-      tc::mbar_wait_bounded(bar, phase);  // the MMAs may still be in flight: one more bounded wait
-      break;
-    }
+    if (!tc::mbar_wait_or_abort(bar, phase, abort_flag)) break;
     phase ^= 1u;
     tc::fence_after_sync();
-    // epilogue: 16 accumulator columns (8 complex outputs) at a time
-    const float fsc = ldexpf(M.sigma, e - 14);
-    const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < 2 * nout; c0 += 16) {
       R acc[16];
       float v[16];
       tc::tmem_ld16(lane_base + (uint32_t)((S - 1) * Np + c0), v);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) tc_init(acc[i], v[i]);
+      for (int k = 0; k < 16; ++k) tc_init(acc[k], v[k]);
 #pragma unroll
       for (int l = S - 2; l >= 0; --l) {
         tc::tmem_ld16(lane_base + (uint32_t)(l * Np + c0), v);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) tc_horner(acc[i], v[i]);
+        for (int k = 0; k < 16; ++k) tc_horner(acc[k], v[k]);
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int o = c0 / 2 + i;
+      for (int k = 0; k < 8; ++k) {
+        const int o = c0 / 2 + k;
         if (o >= nout) break;
-        const cx<R> y{tc_scale(acc[2 * i], fsc), tc_scale(acc[2 * i + 1], fsc)};
+        const cx<R> y{tc_scale(acc[2 * k], fsc), tc_scale(acc[2 * k + 1], fsc)};
         if (!final) {
           out[field * fstride + lbase + o * bsa + m] = y;
         } else {
           const int bidx = gbase + o * gsa;
-          const R sc = RT<R>::from(scale);
           box_store<R>(ore, bidx, m, B3, y.re * sc);
           if (!realx) box_store<R>(oim, bidx, m, B3, y.im * sc);
         }
       }
     }
-    // the next tile's MMAs overwrite the accumulators and operands
+    // the next tile's MMAs overwrite the accumulators once every thread has read them
     tc::fence_before_sync();
     __syncthreads();
+  }
+  // drain: `bar` flips once every MMA issued so far has completed (bounded)
+  if (threadIdx.x == 0) {
+    tc::mma_commit(bar);
+    tc::mbar_wait_bounded(bar, phase);
   }
   if (*abort_flag && threadIdx.x == 0) atomicExch(status, 1);
   tc::fence_before_sync();

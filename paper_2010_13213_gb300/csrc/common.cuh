@@ -214,6 +214,29 @@ LGF_D cx<df> cmac_lazy(cx<df> acc, cx<df> a, cx<df> b) {
           df_dot2_acc_lazy(acc.im, a.re, b.im, a.im, b.re, 1.0f)};
 }
 
+// Real-coefficient accumulations (block-index DFTs by conjugate pairs): acc + a b and acc + a b + sgn c d.
+LGF_D double rfma(double acc, double a, double b) { return fma(a, b, acc); }
+LGF_D float rfma(float acc, float a, float b) { return fmaf(a, b, acc); }
+LGF_D df rfma(df acc, df a, df b) {  // unnormalised (callers renormalise at the end)
+  const float p = __fmul_rn(a.hi, b.hi);
+  float x = __fmaf_rn(a.hi, b.hi, -p);
+  x = __fmaf_rn(a.lo, b.hi, x);
+  x = __fmaf_rn(a.hi, b.lo, x);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  return df{s, __fadd_rn(__fadd_rn(acc.lo, x), t)};
+}
+LGF_D double rdot2(double acc, double a, double b, double c, double d, float sgn) {
+  return fma(a, b, fma((double)sgn * c, d, acc));
+}
+LGF_D float rdot2(float acc, float a, float b, float c, float d, float sgn) { return fmaf(a, b, fmaf(sgn * c, d, acc)); }
+LGF_D df rdot2(df acc, df a, df b, df c, df d, float sgn) { return df_dot2_acc_lazy(acc, a, b, c, d, sgn); }
+template <class R>
+LGF_D R rnorm(R a) { return a; }
+template <>
+LGF_D df rnorm<df>(df a) { return df_renorm(a); }
+
 // Twiddles W_64^j = cos(2 pi j / 64) - i sin(2 pi j / 64), j < 64, passed by value as a kernel
 // parameter (constant bank, broadcast to the warp).  Built on the host from sincospi in FP64.
 template <class R>
@@ -259,7 +282,10 @@ LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
       for (int j = 0; j < len / 2; ++j) {
         cx<R> u = x[i + j];
         cx<R> v = x[i + j + len / 2];
-        if (j != 0) v = cmul(v, twiddle<R, 64, INV>(tw, j * (64 / len)));
+        if (j * (64 / len) == 16)  // W = -i (forward) or +i (inverse): an exact swap
+          v = INV ? cx<R>{-v.im, v.re} : cx<R>{v.im, -v.re};
+        else if (j != 0)
+          v = cmul(v, twiddle<R, 64, INV>(tw, j * (64 / len)));
         x[i + j] = cadd(u, v);
         x[i + j + len / 2] = csub(u, v);
       }

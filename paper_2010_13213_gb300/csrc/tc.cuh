@@ -86,6 +86,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parit
   return true;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+// Bounded wait that also gives up as soon as *abort is set by another thread of the CTA.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, volatile int *abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(mbar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > (1ll << 31)) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
 // 32 lanes x 16 columns of 32-bit accumulators: thread i of the warp gets lane (quadrant base + i),
 // columns [col, col + 16).  Follow with wait_ld before using the values.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
