@@ -32,8 +32,12 @@ struct BoxGeom {
   int nb[3];    // box blocks per axis
   int P[3];     // 2 nb
   int64_t bs[3];  // block strides (in blocks) of the full P-array: 1, Px, Px*Py
-  int pxu;      // block frequencies K1x kept: Px, or Px/2 + 1 for a real field (Hermitian symmetry)
+  int nc;       // fields [0, nc) of a launch are complex (K1x < Px); the others are real fields kept on
+                // the Hermitian half K1x <= Px/2
 };
+// Block frequencies K1x a field keeps, and the most any field of the launch keeps.
+LGF_HD int box_pxu(const BoxGeom &g, int field) { return field < g.nc ? g.P[0] : g.P[0] / 2 + 1; }
+LGF_HD int box_pxmax(const BoxGeom &g) { return g.nc > 0 ? g.P[0] : g.P[0] / 2 + 1; }
 
 // Source of the first forward pass: box block -> buffer block (gather, -1 = absent), a field
 // (dtype per load_field, the component already applied to the pointer) and an optional cell mask.
@@ -111,7 +115,9 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
   const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
-  const bool realx = ax == 0 && g.pxu < P;
+  const int pxf = box_pxu(g, field);
+  if (ax != 0 && l1 >= pxf) return;  // a line beyond this field's K1x range (l1 is K1x for y and z)
+  const bool realx = ax == 0 && pxf < P;
   const int q0 = chunk * CH;
   const int nq = min(CH, half + 1 - q0);  // pair slots q = 0 .. P/2
   for (int i = threadIdx.x; i < nb * CH; i += NT) {
@@ -227,7 +233,9 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
   const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
-  const bool realx = ax == 0 && g.pxu < P;
+  const int pxf = box_pxu(g, field);
+  if (ax != 0 && l1 >= pxf) return;  // a line beyond this field's K1x range (l1 is K1x for y and z)
+  const bool realx = ax == 0 && pxf < P;
   const int o0 = chunk * CH;
   const int no = min(CH, nb - o0);
   for (int i = threadIdx.x; i < (half + 1) * CH; i += NT) {
@@ -389,9 +397,11 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
   extern __shared__ unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
   __shared__ cx<R> T[3][B];
-  // K1 block: blockIdx.x runs over K1x < pxu (all of Px, or Px/2 + 1 for a real field)
-  const int k1x = (int)(blockIdx.x % g.pxu), k1y = (int)((blockIdx.x / g.pxu) % g.P[1]);
-  const int k1z = (int)(blockIdx.x / ((unsigned)g.pxu * g.P[1]));
+  // K1 block: blockIdx.x runs over K1x < the launch's widest range; a real field stops at Px/2
+  const int pxm = box_pxmax(g);
+  const int k1x = (int)(blockIdx.x % pxm), k1y = (int)((blockIdx.x / pxm) % g.P[1]);
+  const int k1z = (int)(blockIdx.x / ((unsigned)pxm * g.P[1]));
+  if (k1x >= box_pxu(g, blockIdx.y)) return;
   const int64_t kb = k1x + (int64_t)g.P[0] * (k1y + (int64_t)g.P[1] * k1z);  // linear in the full P array
   const int Pcx = g.P[0] * B, Pcy = g.P[1] * B, Pcz = g.P[2] * B;
   if (threadIdx.x < 3 * B) {

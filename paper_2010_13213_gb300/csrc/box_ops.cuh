@@ -1,5 +1,6 @@
 // box_ops.cuh -- host launch sequence of one block-index-FFT convolution (instantiated per arithmetic).
 #pragma once
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -55,7 +56,7 @@ struct BoxOps {
   static int convolve(int B, const BoxSpec *S, int nf, const int *nin, const InSpec3 *in,
                       const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1,
                       cudaStream_t st, void (*mark)(void *, int) = nullptr, void *mark_ctx = nullptr,
-                      int slices = 0, int *status = nullptr);
+                      int slices = 0, int *status = nullptr, int64_t *launches = nullptr);
 };
 
 // Launch of one tensor-core pass: persistent CTAs of 128 threads, as many per SM as registers, shared
@@ -121,7 +122,7 @@ static int tc_pass(int slices, const cx<R> *in, cx<R> *out, int64_t fstride, con
 }
 
 template <class R, int B>
-static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real, const int *nin,
+static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, const int *nin,
                      const InSpec3 *in, const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0,
                      cx<R> *Y1, cudaStream_t st, void (*mark)(void *, int), void *mark_ctx, int slices,
                      int *status) {
@@ -134,10 +135,11 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real
   g.bs[0] = 1;
   g.bs[1] = g.P[0];
   g.bs[2] = (int64_t)g.P[0] * g.P[1];
-  g.pxu = real ? g.P[0] / 2 + 1 : g.P[0];
+  g.nc = nc;
   const int *nb = g.nb, *P = g.P;
   const int64_t fstride = (int64_t)P[0] * P[1] * P[2] * B3;
-  const int64_t nmid = (int64_t)g.pxu * P[1] * P[2];
+  const int pxu = box_pxmax(g);  // lines of the y and z passes run over the widest K1x range
+  const int64_t nmid = (int64_t)pxu * P[1] * P[2];
   const size_t sm = sizeof(cx<R>) * (size_t)B * B * (B + 1);
   static bool attr = false;
   if (!attr) {
@@ -158,40 +160,31 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real
   auto pass = [&](const cx<R> *in_, cx<R> *out_, int ax, int3 ext, int lines, int inverse, int gather, int final,
                   double sc) {
     const int nb_ax = nb[ax];
-    const bool realx = ax == 0 && g.pxu < P[0];
-    const int nout = inverse ? nb_ax : (realx ? g.pxu : 2 * nb_ax);
-    if (slices > 0) {
+    const int nout = inverse ? nb_ax : 2 * nb_ax;
+    if (slices > 0) {  // tensor-core passes: one kind of field per launch (nc = 0 or n)
+      const bool realx = ax == 0 && nc == 0 && pxu < P[0];
       TcMat M = S->tcm[ax][inverse ? (realx ? 2 : 1) : 0];
       if (realx && !inverse) {  // the first pxu outputs of the forward matrix
-        M.nout = g.pxu;
-        M.Np = (2 * g.pxu + 15) / 16 * 16;
+        M.nout = pxu;
+        M.Np = (2 * pxu + 15) / 16 * 16;
       }
       const int r = tc_pass<R, B>(slices, in_, out_, fstride, g, ax, ext, M, gather, final, n, lines, sp, outs, sc,
                                   status, st);
       if (r && !rc) rc = r;
       return;
     }
+    // one cell per thread: more resident warps to cover the loads (the passes are latency-bound)
     constexpr int NT = 128;
     if (!inverse) {
-      const int slots = nb_ax + 1;  // conjugate pairs q = 0 .. P/2
-      if (slots <= 4) {
-        k_bdft_fwd<R, B, 4, 2, NT><<<dim3(B3 / (2 * NT), lines, n), NT, 0, st>>>(
-            in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, 1, sp);
-      } else {
-        const int nch = (slots + 3) / 4;
-        k_bdft_fwd<R, B, 4, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
-            in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, nch, sp);
-      }
-    } else if (nout <= 8) {
-      k_bdft_inv<R, B, 8, 2, NT><<<dim3(B3 / (2 * NT), lines, n), NT, 0, st>>>(
-          in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, 1, outs, sc);
+      const int nch = (nb_ax + 1 + 3) / 4;  // conjugate pair slots q = 0 .. P/2, four per chunk
+      k_bdft_fwd<R, B, 4, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+          in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, nch, sp);
     } else {
       const int nch = (nout + 7) / 8;
       k_bdft_inv<R, B, 8, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
           in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, nch, outs, sc);
     }
   };
-  const int pxu = g.pxu;
   // forward x (gather), y, z; kernel; inverse z, y, x (scatter)
   pass(nullptr, Y0, 0, make_int3(0, nb[1], nb[2]), nb[1] * nb[2], 0, 1, 0, 1.0);
   pass(Y0, Y1, 1, make_int3(pxu, 0, nb[2]), pxu * nb[2], 0, 0, 0, 1.0);
@@ -211,19 +204,29 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, bool real
 template <class R, int B>
 static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec3 *in, const OutSpec<R> *ore,
                           const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1, cudaStream_t st,
-                          void (*mark)(void *, int), void *mark_ctx, int slices, int *status) {
+                          void (*mark)(void *, int), void *mark_ctx, int slices, int *status, int64_t *launches) {
   std::vector<int> cplx, real;
   for (int f = 0; f < nf; ++f) {
     const bool is_real = nin[f] == 1 && in[f].s[0].part == 0 && oim[f].scatter == nullptr;
     (is_real ? real : cplx).push_back(f);
   }
-  for (int pass = 0; pass < 2; ++pass) {
-    const std::vector<int> &lst = pass ? real : cplx;
+  // CUDA-core passes take complex and real fields in one launch per stage (complex first); the
+  // tensor-core passes keep the two kinds apart (their coefficient matrices differ)
+  std::vector<std::vector<int>> lists;
+  if (slices > 0) {
+    lists = {cplx, real};
+  } else {
+    lists.push_back(cplx);
+    lists[0].insert(lists[0].end(), real.begin(), real.end());
+  }
+  for (const std::vector<int> &lst : lists) {
     for (size_t f0 = 0; f0 < lst.size(); f0 += BOX_MAXF) {
       std::vector<int> grp(lst.begin() + f0, lst.begin() + std::min(lst.size(), f0 + BOX_MAXF));
-      int rc = box_group<R, B>(S, grp, pass == 1, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices,
-                               status);
+      int nc = 0;
+      for (int f : grp) nc += std::find(cplx.begin(), cplx.end(), f) != cplx.end();
+      int rc = box_group<R, B>(S, grp, nc, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status);
       if (rc) return rc;
+      if (launches) *launches += 7;
     }
   }
   cudaError_t e = cudaGetLastError();
@@ -233,13 +236,16 @@ static int box_convolve_b(const BoxSpec *S, int nf, const int *nin, const InSpec
 template <class R>
 int BoxOps<R>::convolve(int B, const BoxSpec *S, int nf, const int *nin, const InSpec3 *in,
                         const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0, cx<R> *Y1,
-                        cudaStream_t st, void (*mark)(void *, int), void *mark_ctx, int slices, int *status) {
+                        cudaStream_t st, void (*mark)(void *, int), void *mark_ctx, int slices, int *status,
+                        int64_t *launches) {
   if (slices > 0 && (std::is_same<R, double>::value || !status))
     return set_error(LGF_E_UNSUPPORTED, "the tensor-core DFT-GEMM runs in FP32 or double-float only");
   if (B == 8)
-    return box_convolve_b<R, 8>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status);
+    return box_convolve_b<R, 8>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status,
+                                launches);
   if (B == 16)
-    return box_convolve_b<R, 16>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status);
+    return box_convolve_b<R, 16>(S, nf, nin, in, ore, oim, scale, Y0, Y1, st, mark, mark_ctx, slices, status,
+                                 launches);
   return set_error(LGF_E_UNSUPPORTED, "block size %d", B);
 }
 

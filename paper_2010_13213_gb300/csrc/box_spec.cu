@@ -127,7 +127,7 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
   g.bs[0] = 1;
   g.bs[1] = g.P[0];
   g.bs[2] = (int64_t)g.P[0] * g.P[1];
-  g.pxu = g.P[0];
+  g.nc = 1;
   const int64_t nblk = (int64_t)g.P[0] * g.P[1] * g.P[2];
   const int64_t n = nblk * B3;
   cx<double> *Y0 = nullptr, *Y1 = nullptr, *wP[3] = {nullptr, nullptr, nullptr};

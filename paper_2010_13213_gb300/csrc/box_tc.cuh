@@ -137,7 +137,6 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   const int gs1 = a1 == 0 ? 1 : g.nb[0];
   const int gs2 = a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1];
-  const bool realx = ax == 0 && g.pxu < g.P[0];
   const int ntiles = nfield * lines * NCH;
   const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, Np);
   const uint32_t a_base = tc::smem_addr(smem + pl.a_off), b_base = tc::smem_addr(smem + pl.b_off);
@@ -146,6 +145,9 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
   for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
     const int chunk = tile % NCH, line = (tile / NCH) % lines, field = tile / (NCH * lines);
     const int l1 = line % e1, l2 = line / e1;
+    const int pxf = box_pxu(g, field);
+    if (ax != 0 && l1 >= pxf) continue;  // beyond this field's K1x range (uniform over the CTA)
+    const bool realx = ax == 0 && pxf < g.P[0];
     const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
     const int gbase = l1 * gs1 + l2 * gs2;
     const int m = chunk * TC_ROWS + row;

@@ -283,9 +283,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       }
       const int nf = (int)nin.size();
       if ((rc = BoxOps<R>::convolve(B, S, nf, nin.data(), in.data(), ore.data(), oim.data(), scale, Y0, Y1, st,
-                                    o.timing ? phase_mark_cb : nullptr, &tm, o.dft_slices, t->d_status)))
+                                    o.timing ? phase_mark_cb : nullptr, &tm, o.dft_slices, t->d_status, &launches)))
         return rc;
-      launches += 7 * ((nf + BOX_MAXF - 1) / BOX_MAXF);
       target_cells += L.n_omega;
       nsrc_total += nSA + nSB;
       ntgt_total += nT;

@@ -232,11 +232,11 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
     ore[fi] = OutSpec<R>{smap, nullptr, phi, nullptr, nullptr, c0 * cs, dtype, 0};
     oim[fi] = c1 < ncomp ? OutSpec<R>{smap, nullptr, phi, nullptr, nullptr, c1 * cs, dtype, 0} : OutSpec<R>{};
   }
+  int64_t launches = 0;
   if ((rc = BoxOps<R>::convolve(B, S, nf, nin.data(), in.data(), ore.data(), oim.data(), scale,
                                 (cx<R> *)ws->buf[0].p, (cx<R> *)ws->buf[1].p, st,
-                                o.timing ? phase_mark_cb : nullptr, &tm, o.dft_slices, t->d_status)))
+                                o.timing ? phase_mark_cb : nullptr, &tm, o.dft_slices, t->d_status, &launches)))
     return rc;
-  const int64_t launches = 7 * ((nf + BOX_MAXF - 1) / BOX_MAXF);
   tm.finish(rep);
   fill_report(rep, P, B3, ws, launches, LGF_MAC_BOX, (int64_t)S->bytes);
   if (o.timing) {
