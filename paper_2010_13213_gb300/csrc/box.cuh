@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
                                                     const cx<R> *__restrict__ twz, Tw64<R> tw,
                                                     R *__restrict__ kout) {
   constexpr int B3 = B * B * B, RS = B + 1;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
   __shared__ cx<R> T[3][B];
   // K1 block: blockIdx.x runs over K1x < the launch's widest range; a real field stops at Px/2

@@ -90,8 +90,10 @@ struct RT<df> {
 };
 
 // ------------------------------------------------------------------ complex
+// Aligned to its size so that a complex value moves as one 8- or 16-byte access (every array of cx is
+// allocated by cudaMalloc or declared as cx, so element addresses keep this alignment).
 template <class R>
-struct cx {
+struct alignas(2 * sizeof(R)) cx {
   R re, im;
 };
 template <class R>

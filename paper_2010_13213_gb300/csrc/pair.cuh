@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_block_fwd(const void *__restrict__ f, i
                                                    const uint8_t *__restrict__ cellmask, int bits,
                                                    Tw64<R> tw) {
   using G = PairGeom<B>;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *A1 = reinterpret_cast<cx<R> *>(smem_raw);
   cx<R> *A2 = A1 + G::A1;
   const int comp = blockIdx.y;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_block_inv(const cx<R> *__restrict__ spe
                                                    const uint8_t *__restrict__ cellmask, int bits,
                                                    double scale, Tw64<R> tw) {
   using G = PairGeom<B>;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *A1 = reinterpret_cast<cx<R> *>(smem_raw);
   cx<R> *A2 = A1 + G::A1;
   const int comp = blockIdx.y;
