@@ -157,28 +157,33 @@ def df_box_instructions(B, nb, ncomp):
     return dft, mid
 
 
-def roofline_entry(case, B, ncomp, rep, ph):
-    """Roofline of the dominant kernel class of the DF32 solve (FP32-pipe bound)."""
-    W = (2 * B) ** 2 * (B + 1)
-    if rep.mac_mode_used == 1:  # pair
-        cmacs = rep.pairs * W * ncomp
-        inst = cmacs * DF_OPS_PER_CMAC
-        ms = ph[3]
-        kern, launches = "k_mac_pair<df,4,3> (block-pair multiply-accumulate)", 1
-    else:
-        nz, ny, nx = (n // B for n in case["shape"])
-        ngroups = (1 if ncomp // 2 else 0) + (1 if ncomp % 2 else 0)
-        dft, local = df_box_instructions(B, (nx, ny, nz), ncomp)
-        if ph[3] >= ph[2] + ph[4]:
-            inst, ms, kern, launches = local, ph[3], "k_box_mid<df,16> (twiddle + local FFT + kernel + inverse)", ngroups
-        else:
-            inst, ms, kern, launches = dft, ph[2] + ph[4], "k_bdft_fwd/inv<df,16> (block-index DFT passes)", 6 * ngroups
+# DRAM bytes (read + write) of one k_box_mid<df,16> launch on this workload, from one ncu capture of
+# the current kernel (set to None when the kernel changes)
+MID_DF16_TRAFFIC = 125.098496e6 + 32.073216e6
+
+
+def _alu_entry(kern, inst, ms, launches, traffic=None):
     ach = inst / (ms * 1e-3)
     return {"kernel": kern, "bound": "alu", "achieved": ach / 1e12, "peak": FP32_INST_PEAK / 1e12,
-            "unit": "T FP32-inst/s", "frac": ach / FP32_INST_PEAK, "traffic": None,
+            "unit": "T FP32-inst/s", "frac": ach / FP32_INST_PEAK, "traffic": traffic,
             "launches_per_step": launches, "kernel_ms_per_step": float(ms),
-            "note": "algorithmic FP32 instructions of the double-float arithmetic / CUDA-event time of the"
-                    " kernel class; peak = 152 SMs x 128 FP32 lanes x 2070 MHz (derived, not measured)"}
+            "note": "algorithmic FP32 instructions of the double-float arithmetic per step / CUDA-event time"
+                    " of the kernel on its stream; peak = 152 SMs x 128 FP32 lanes x 2070 MHz (derived, not"
+                    " measured); traffic = ncu DRAM read + write bytes of one launch"}
+
+
+def roofline_entry(case, B, ncomp, rep, ph):
+    """Roofline of the dominant kernel of the DF32 solve (FP32-pipe bound), and of the second kernel class."""
+    W = (2 * B) ** 2 * (B + 1)
+    if rep.mac_mode_used == 1:  # pair
+        inst = rep.pairs * W * ncomp * DF_OPS_PER_CMAC
+        return _alu_entry("k_mac_pair<df,4,3> (block-pair multiply-accumulate)", inst, ph[3], 1), None
+    nz, ny, nx = (n // B for n in case["shape"])
+    dft, local = df_box_instructions(B, (nx, ny, nz), ncomp)
+    mid = _alu_entry("k_box_mid<df,16> (twiddle + local FFT + kernel + inverse, all fields)", local, ph[3], 1,
+                     MID_DF16_TRAFFIC if (B, nx, ny, nz, ncomp) == (16, 6, 6, 3, 3) else None)
+    passes = _alu_entry("k_bdft_fwd/inv<df,16> (six block-index DFT passes)", dft, ph[2] + ph[4], 6)
+    return mid, passes
 
 
 def build_case():
@@ -323,7 +328,7 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    roof = roofline_entry(case, B, ncomp, rep_df, ph_df)
+    roof, roof_passes = roofline_entry(case, B, ncomp, rep_df, ph_df)
     cores = os.cpu_count()
     t0 = time.perf_counter()
     cpu_oracle_step(case)
@@ -350,6 +355,7 @@ def run_gpu(args):
         "phases_ms_df32": _phases(ph_df),
         "table_build_s": t_tab,
         "roofline": roof,
+        "roofline_second": roof_passes,
         "cpu_baseline": {"value": cells / cpu_dt / 1e6, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
                          "sample": "full workload once: zero-padded FP64 FFT convolution (pocketfft)",
                          "threads_used": oracle.num_threads()},

@@ -189,6 +189,14 @@ int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f
  */
 int lgf_device_status(lgf_table *t);
 
+/*
+ * lgf_selftest_wait_timeout -- launch one CTA that waits on an mbarrier no thread ever arrives at, with
+ * the bounded wait of the tensor-core kernels limited to 2^log2_cycles SM cycles (10..31).  The wait
+ * gives up, the kernel sets the table's status word and returns; a following lgf_device_status reports
+ * LGF_E_TIMEOUT and clears it.  Checks the timeout path without faulting or hanging the GPU.
+ */
+int lgf_selftest_wait_timeout(lgf_table *t, int32_t log2_cycles, void *cuda_stream);
+
 /* ---- batches: many independent instances solved as one unit, capturable into a CUDA graph */
 typedef struct lgf_batch lgf_batch; /* opaque */
 

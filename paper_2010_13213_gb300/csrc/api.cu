@@ -9,6 +9,7 @@
 #include <tuple>
 
 #include "internal.h"
+#include "tc.cuh"
 #include "solver.h"
 
 namespace lgf {
@@ -100,9 +101,33 @@ int take_device_status(lgf_table *t) {
   return set_error(LGF_E_TIMEOUT, "a bounded device-side wait gave up (tensor-core DFT-GEMM)");
 }
 
+// A wait that cannot complete: an mbarrier expecting one arrival that never comes, waited on with the
+// bounded helper of the tensor-core kernels (limit 2^log2_cycles cycles).  It must give up, set the
+// status word and leave the context usable.
+__global__ void k_wait_selftest(int *status, long long limit) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const bool ok = tc::mbar_wait_or_abort(&bar, 0, &abort_flag, limit);
+  __syncthreads();
+  if (threadIdx.x == 0 && (!ok || abort_flag)) atomicExch(status, 1);
+}
+
 }  // namespace lgf
 
 extern "C" {
+
+int lgf_selftest_wait_timeout(lgf_table *t, int32_t log2_cycles, void *cuda_stream) {
+  if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");
+  if (log2_cycles < 10 || log2_cycles > 31) return set_error(LGF_E_INVALID_ARG, "log2_cycles %d", log2_cycles);
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)cuda_stream>>>(t->d_status, 1ll << log2_cycles);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "self-test launch: %s", cudaGetErrorString(e));
+}
 
 int lgf_device_status(lgf_table *t) {
   if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");

@@ -89,12 +89,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parit
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
-// Bounded wait that also gives up as soon as *abort is set by another thread of the CTA.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, volatile int *abort) {
+// Bounded wait that also gives up as soon as *abort is set by another thread of the CTA; the limit is
+// 2^31 cycles (about a second) unless given.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *mbar, uint32_t parity, volatile int *abort,
+                                                   long long limit = 1ll << 31) {
   const long long t0 = clock64();
   while (!mbar_try_wait(mbar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > (1ll << 31)) {
+    if (clock64() - t0 > limit) {
       *abort = 1;
       return false;
     }

@@ -90,12 +90,13 @@ def load():
         lib.lgf_batch_graph_launch.argtypes = [c_void_p, c_void_p]
         lib.lgf_batch_graph_nodes.argtypes = [c_void_p, POINTER(c_int64)]
         lib.lgf_device_status.argtypes = [c_void_p]
+        lib.lgf_selftest_wait_timeout.argtypes = [c_void_p, c_int32, c_void_p]
         lib.lgf_last_error.restype = c_char_p
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
                      "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_batch_create", "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
-                     "lgf_device_status"):
+                     "lgf_device_status", "lgf_selftest_wait_timeout"):
             getattr(lib, name).restype = c_int32
         _LIB = lib
     return _LIB
@@ -159,6 +160,10 @@ def _opts(precision=LGF_PREC_FP64, mac_mode=LGF_MAC_AUTO, residual=0, timing=0, 
 def lgf_device_status(table) -> None:
     """Synchronise and raise LgfError(LGF_E_TIMEOUT) if a bounded device wait gave up since the last read."""
     _check(load().lgf_device_status(c_void_p(table)))
+
+
+def lgf_selftest_wait_timeout(table, log2_cycles: int = 24, cuda_stream: int = 0) -> None:
+    _check(load().lgf_selftest_wait_timeout(c_void_p(table), int(log2_cycles), c_void_p(cuda_stream or None)))
 
 
 def lgf_poisson_solve(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, dtype: int = LGF_F64,

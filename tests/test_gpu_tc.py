@@ -148,3 +148,20 @@ def test_tc_rejects_bad_slices(L, tables):
         with pytest.raises(L.LgfError) as e:
             solve(L, tables[16], [case["blocks"]], 16, case["h"], case["f"], prec, sl)
         assert e.value.status in (L.LGF_E_INVALID_ARG, L.LGF_E_UNSUPPORTED)
+
+
+def test_bounded_wait_gives_up_and_context_survives(L, tables):
+    """A wait on an mbarrier nothing arrives at (limit 2^24 cycles) reports LGF_E_TIMEOUT through the
+    status word; the word clears and the next solve is unaffected."""
+    L.lgf_device_status(tables[16])  # clean start
+    L.lgf_selftest_wait_timeout(tables[16], 24)
+    with pytest.raises(L.LgfError) as e:
+        L.lgf_device_status(tables[16])
+    assert e.value.status == L.LGF_E_TIMEOUT
+    L.lgf_device_status(tables[16])  # cleared
+    case = S.single_level_random(n=32, B=16, seed=5, ncomp=2)
+    ref = oracle.solve_box_fft(case["box"], case["h"])
+    phi = solve(L, tables[16], [case["blocks"]], 16, case["h"], case["f"], 2, 5)
+    got = S.blocks_to_box(phi, case["blocks"], 16, case["shape"])
+    assert max(rel(got[c], ref[c]) for c in range(2)) <= TOL[(2, 5)]
+    L.lgf_device_status(tables[16])
