@@ -378,9 +378,19 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
 }
 
 // ------------------------------------------------------------------ fused twiddle + local FFT + kernel
-// One CTA per (K1 block, field): Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat[K1][.]; back.
-// The inverse runs as conj(FFT(conj(.))) so one FFT body serves all six axis passes (small code,
-// no instruction-cache stalls).  Shared memory: B^3 complex with x rows padded to B+1.
+// One CTA of B^2 threads per (K1 block, field): Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat;
+// back.  Six line-FFT steps, thread t owning line (l0, l1) = (t % B, t / B) of each axis:
+//   0  z lines (x, y): global Y, twiddle, FFT_z              -> shared
+//   1  y lines (x, z): FFT_y                                 -> shared
+//   2  x lines (y, z): FFT_x, X Ghat, conjugate              (registers)
+//   3  x lines      : FFT_x                                  -> shared
+//   4  y lines      : FFT_y                                  -> shared
+//   5  z lines      : FFT_z, conjugate, conjugate twiddle    -> global Y
+// (the inverse is conj(FFT(conj(.))), so one FFT body serves every step: small code, no
+// instruction-cache stalls).  Four barriers, one shared store and load per cell and step.  Ghat is stored
+// per block as [x][z][y] so the x lines of step 2 read it coalesced.  Shared memory: B^3 complex with
+// rows padded to B + 1 (every line direction conflict-free).  Without MULTIPLY (kernel-spectrum
+// generation) the real part of step 2 goes to `kout` in the same [x][z][y] order.
 template <int B>
 struct MidGeom {
   static constexpr int RS = B + 1;          // padded row
@@ -393,7 +403,7 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
                                                     const cx<R> *__restrict__ twx, const cx<R> *__restrict__ twy,
                                                     const cx<R> *__restrict__ twz, Tw64<R> tw,
                                                     R *__restrict__ kout) {
-  constexpr int B3 = B * B * B, RS = B + 1;
+  constexpr int B2 = B * B, B3 = B * B * B, RS = B + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
   __shared__ cx<R> T[3][B];
@@ -413,57 +423,44 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
   }
   __syncthreads();
   cx<R> *Yb = Y + blockIdx.y * fstride + kb * B3;  // field blockIdx.y
-  // element-wise loops: thread t owns cells (x, y) = (t % B, t / B) of every z plane (B*B <= 256)
-  const int ex = threadIdx.x % B, ey = (threadIdx.x / B) % B;
-  const int zstep = blockDim.x / (B * B);
-  const int z0 = threadIdx.x / (B * B);
-  {
-    const cx<R> txy = cmul(T[0][ex], T[1][ey]);
-    for (int z = z0; z < B; z += zstep) {
-      const cx<R> w = cmul(txy, T[2][z]);
-      S[(z * B + ey) * RS + ex] = cmul(Yb[(z * B + ey) * B + ex], w);
-    }
-  }
-  const int npass = MULTIPLY ? 6 : 3;
-  for (int pass = 0; pass < npass; ++pass) {
-    __syncthreads();
-    if (pass == 3) {
-      // X *= Ghat (real), then conjugate: the inverse is conj(FFT(conj(X Ghat)))
-      for (int z = z0; z < B; z += zstep) {
-        cx<R> &v = S[(z * B + ey) * RS + ex];
-        const R gk = Gh[kb * B3 + (z * B + ey) * B + ex];
-        v = cx<R>{v.re * gk, -(v.im * gk)};
-      }
-      __syncthreads();
-    }
-    const int ax = pass % 3;
-    for (int line = threadIdx.x; line < B * B; line += blockDim.x) {
-      const int l0 = line % B, l1 = line / B;
-      int base, stride;
-      if (ax == 0) base = (l1 * B + l0) * RS, stride = 1;             // x lines: (y, z) = (l0, l1)
-      else if (ax == 1) base = l1 * B * RS + l0, stride = RS;         // y lines: (x, z) = (l0, l1)
-      else base = l1 * RS + l0, stride = B * RS;                      // z lines: (x, y) = (l0, l1)
-      cx<R> v[B];
+  const int t = threadIdx.x, l0 = t % B, l1 = t / B;
+  const cx<R> txy = cmul(T[0][l0], T[1][l1]);  // twiddle of the z line (x, y) = (l0, l1) without z
+  cx<R> v[B];
+  const int nstep = MULTIPLY ? 6 : 3;
+  for (int step = 0; step < nstep; ++step) {
+    const int ax = step < 3 ? 2 - step : step - 3;
+    int base, stride;
+    if (ax == 0) base = (l1 * B + l0) * RS, stride = 1;             // x lines: (y, z) = (l0, l1)
+    else if (ax == 1) base = l1 * B * RS + l0, stride = RS;         // y lines: (x, z) = (l0, l1)
+    else base = l1 * RS + l0, stride = B * RS;                      // z lines: (x, y) = (l0, l1)
+    if (step == 0) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) v[i] = cmul(Yb[(i * B + l1) * B + l0], cmul(txy, T[2][i]));
+    } else if (step != 3) {
 #pragma unroll
       for (int i = 0; i < B; ++i) v[i] = S[base + i * stride];
-      fft_reg<R, B, false>(v, tw);
-      if (!MULTIPLY && ax == 2) {
-        // kernel-spectrum generation: store the real part (G even => X real); l0 = x, l1 = y
+    }
+    fft_reg<R, B, false>(v, tw);
+    if (step == 2) {
+      if (!MULTIPLY) {
 #pragma unroll
-        for (int i = 0; i < B; ++i) kout[kb * B3 + (i * B + l1) * B + l0] = v[i].re;
+        for (int i = 0; i < B; ++i) kout[kb * B3 + i * B2 + t] = v[i].re;
       } else {
 #pragma unroll
-        for (int i = 0; i < B; ++i) S[base + i * stride] = v[i];
+        for (int i = 0; i < B; ++i) {
+          const R gk = Gh[kb * B3 + i * B2 + t];
+          v[i] = cx<R>{v[i].re * gk, -(v[i].im * gk)};
+        }
       }
+      continue;
     }
-  }
-  if (!MULTIPLY) return;
-  __syncthreads();
-  {
-    const cx<R> txy = conj(cmul(T[0][ex], T[1][ey]));
-    for (int z = z0; z < B; z += zstep) {
-      const cx<R> w = cmul(txy, conj(T[2][z]));
-      Yb[(z * B + ey) * B + ex] = cmul(conj(S[(z * B + ey) * RS + ex]), w);
+    if (step == 5) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) Yb[(i * B + l1) * B + l0] = conj(cmul(v[i], cmul(txy, T[2][i])));
+    } else {
+#pragma unroll
+      for (int i = 0; i < B; ++i) S[base + i * stride] = v[i];
+      __syncthreads();
     }
   }
 }
