@@ -113,18 +113,19 @@ CADD, CNORM, CMUL, DFMUL, RFMA, DOT2, DFADD = 16, 6, 38, 7, 12, 24, 14  # FP32 i
 
 
 def _fwd_pass_inst(nb, lines, B3, both):
-    """Conjugate-pair forward block-index DFT of nb inputs to P = 2 nb outputs (k_bdft_fwd): slots q = 0
-    and q = nb take sums, the nb - 1 pairs accumulate A, B with real coefficients; `both`: store X_k and
-    X_{P-k} (False: the Hermitian half of a real field)."""
-    per = (nb + 1) * CADD + (nb - 1) * (2 * CADD + (nb - 1) * 4 * RFMA)
+    """Conjugate-pair forward block-index DFT of nb inputs to P = 2 nb outputs (k_bdft_fwd): the j = 0
+    term initialises the accumulators, slots q = 0 and q = nb are sums, the nb - 1 general pairs take
+    four real multiply-adds per input; `both`: store X_k and X_{P-k} (False: the Hermitian half)."""
+    per = (nb - 1) * (2 * CADD + (nb - 1) * 4 * RFMA)
     per += 2 * CNORM + (nb - 1) * (2 if both else 1) * 2 * DFADD
     return lines * B3 * per
 
 
 def _inv_pass_inst(nb, lines, B3, real):
-    """Conjugate-pair inverse of P = 2 nb inputs to nb outputs (k_bdft_inv): per input pair U, V (two
-    complex adds) then a two-term real dot product per output part (one part for a real field)."""
-    per = 2 * nb * CADD + (nb - 1) * (2 * CADD + CADD + (nb - 1) * (1 if real else 2) * DOT2) + nb * CNORM
+    """Conjugate-pair inverse of P = 2 nb inputs to nb outputs (k_bdft_inv): X_0 +- X_{P/2} per output,
+    then per general input pair U, V (two complex adds) and a two-term real dot product per output part
+    (one part for a real field; a sum for output 0)."""
+    per = nb * CADD + (nb - 1) * (2 * CADD + CADD + (nb - 1) * (1 if real else 2) * DOT2) + nb * CNORM
     return lines * B3 * per
 
 

@@ -104,12 +104,12 @@ LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
 // the next input is fetched while the current one multiplies.  The first forward pass (gather) reads
 // through the field's input specs, the last inverse pass (final) writes through its output specs.
 // Field f's arrays start at in + f * fstride, out + f * fstride.
-template <class R, int B, int CH, int CELLS, int NT>
+template <class R, int B, int CH, int NT>
 __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
                                                  int gather, int nchunk, FwdSpecs sp) {
   constexpr int B3 = B * B * B;
-  __shared__ R Tc[BOX_NB_MAX][CH], Ts[BOX_NB_MAX][CH];
+  __shared__ cx<R> TW[BOX_NB_MAX][CH];  // (cos, sin)(2 pi j q / P) of the chunk's general slots
   const int nb = g.nb[ax], P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
@@ -118,15 +118,16 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   const int pxf = box_pxu(g, field);
   if (ax != 0 && l1 >= pxf) return;  // a line beyond this field's K1x range (l1 is K1x for y and z)
   const bool realx = ax == 0 && pxf < P;
-  const int q0 = chunk * CH;
-  const int nq = min(CH, half + 1 - q0);  // pair slots q = 0 .. P/2
+  // general slots q = 1 .. half - 1 in chunks of CH; chunk 0 also sums the slots q = 0 and q = half
+  const int q0 = 1 + chunk * CH;
+  const int nq = max(0, min(CH, half - q0));
+  const bool ends = chunk == 0;
   for (int i = threadIdx.x; i < nb * CH; i += NT) {
     const int j = i / CH, c = i % CH;
     const int n = (int)(((int64_t)j * (q0 + c)) % P);
-    Tc[j][c] = tw.w[n].re;
-    Ts[j][c] = -tw.w[n].im;
+    TW[j][c] = cx<R>{tw.w[n].re, -tw.w[n].im};
   }
-  const int m0 = blockIdx.x * (NT * CELLS) + threadIdx.x;
+  const int m = blockIdx.x * NT + threadIdx.x;
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
@@ -144,90 +145,73 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
       }
   }
   const cx<R> *src = in + field * fstride + lbase;
-  auto fetch = [&](int j, cx<R>(&x)[CELLS]) {
-    if (gather) {
-      const int bidx = gbase + j * gsa;
-#pragma unroll
-      for (int c = 0; c < CELLS; ++c) {
-        const int m = m0 + NT * c;
-        R re = RT<R>::zero(), im = RT<R>::zero();
-        auto add = [&](const InSpec &q) {
-          const int idx = q.gather[bidx];
-          if (idx < 0) return;
-          const int64_t e = (int64_t)idx * B3 + m;
-          if (q.mask && !(q.mask[e] & q.bits)) return;
-          const R v = load_field<R>(q.src, e, q.dtype);
-          if (q.part) im = im + v;
-          else re = re + v;
-        };
-        if (ns > 0) add(s0);
-        if (ns > 1) add(s1);
-        if (ns > 2) add(s2);
-        x[c] = cx<R>{re, im};
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < CELLS; ++c) x[c] = src[j * bsa + m0 + NT * c];
-    }
+  auto fetch = [&](int j) -> cx<R> {
+    if (!gather) return src[j * bsa + m];
+    const int bidx = gbase + j * gsa;
+    R re = RT<R>::zero(), im = RT<R>::zero();
+    auto add = [&](const InSpec &q) {
+      const int idx = q.gather[bidx];
+      if (idx < 0) return;
+      const int64_t e = (int64_t)idx * B3 + m;
+      if (q.mask && !(q.mask[e] & q.bits)) return;
+      const R v = load_field<R>(q.src, e, q.dtype);
+      if (q.part) im = im + v;
+      else re = re + v;
+    };
+    if (ns > 0) add(s0);
+    if (ns > 1) add(s1);
+    if (ns > 2) add(s2);
+    return cx<R>{re, im};
   };
   __syncthreads();
-  cx<R> A[CELLS][CH], Bv[CELLS][CH];
+  // j = 0: every coefficient is 1
+  cx<R> x = fetch(0);
+  cx<R> xn = nb > 1 ? fetch(1) : cx_zero<R>();
+  cx<R> A[CH], Bv[CH];
 #pragma unroll
-  for (int c = 0; c < CELLS; ++c)
-#pragma unroll
-    for (int k = 0; k < CH; ++k) A[c][k] = Bv[c][k] = cx_zero<R>();
-  cx<R> xn[CELLS];
-  fetch(0, xn);
-  for (int j = 0; j < nb; ++j) {
-    cx<R> x[CELLS];
-#pragma unroll
-    for (int c = 0; c < CELLS; ++c) x[c] = xn[c];
-    if (j + 1 < nb) fetch(j + 1, xn);
+  for (int k = 0; k < CH; ++k) {
+    A[k] = x;
+    Bv[k] = cx_zero<R>();
+  }
+  cx<R> S0 = x, Sh = x;  // slot 0 (coefficients 1) and slot half (coefficients (-1)^j)
+  for (int j = 1; j < nb; ++j) {
+    x = xn;
+    if (j + 1 < nb) xn = fetch(j + 1);
+    if (ends) {
+      S0 = cadd(S0, x);
+      Sh = (j & 1) ? csub(Sh, x) : cadd(Sh, x);
+    }
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
-      if (k >= nq) break;
-      const int q = q0 + k;
-      if (j == 0 || q == 0) {
-#pragma unroll
-        for (int c = 0; c < CELLS; ++c) A[c][k] = cadd(A[c][k], x[c]);
-      } else if (q == half) {
-#pragma unroll
-        for (int c = 0; c < CELLS; ++c) A[c][k] = (j & 1) ? csub(A[c][k], x[c]) : cadd(A[c][k], x[c]);
-      } else {
-        const R cc = Tc[j][k], ss = Ts[j][k];
-#pragma unroll
-        for (int c = 0; c < CELLS; ++c) {
-          A[c][k] = cx<R>{rfma(A[c][k].re, cc, x[c].re), rfma(A[c][k].im, cc, x[c].im)};
-          Bv[c][k] = cx<R>{rfma(Bv[c][k].re, ss, x[c].re), rfma(Bv[c][k].im, ss, x[c].im)};
-        }
+      if (k < nq) {
+        const cx<R> w = TW[j][k];
+        A[k] = cx<R>{rfma(A[k].re, w.re, x.re), rfma(A[k].im, w.re, x.im)};
+        Bv[k] = cx<R>{rfma(Bv[k].re, w.im, x.re), rfma(Bv[k].im, w.im, x.im)};
       }
     }
   }
   cx<R> *dst = out + field * fstride + lbase;
+  if (ends) {
+    dst[m] = cnorm(S0);
+    dst[half * bsa + m] = cnorm(Sh);
+  }
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
-    if (k >= nq) break;
-    const int q = q0 + k;
-#pragma unroll
-    for (int c = 0; c < CELLS; ++c) {
-      const int m = m0 + NT * c;
-      if (q == 0 || q == half) {
-        dst[q * bsa + m] = cnorm(A[c][k]);
-      } else {
-        const cx<R> a = A[c][k], b = Bv[c][k];
-        dst[q * bsa + m] = cx<R>{rnorm(a.re + b.im), rnorm(a.im - b.re)};
-        if (!realx) dst[(P - q) * bsa + m] = cx<R>{rnorm(a.re - b.im), rnorm(a.im + b.re)};
-      }
+    if (k < nq) {
+      const int q = q0 + k;
+      const cx<R> a = A[k], b = Bv[k];
+      dst[q * bsa + m] = cx<R>{rnorm(a.re + b.im), rnorm(a.im - b.re)};
+      if (!realx) dst[(P - q) * bsa + m] = cx<R>{rnorm(a.re - b.im), rnorm(a.im + b.re)};
     }
   }
 }
 
-template <class R, int B, int CH, int CELLS, int NT>
+template <class R, int B, int CH, int NT>
 __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
                                                  int final, int nchunk, InvOuts<R> outs, double scale) {
   constexpr int B3 = B * B * B;
-  __shared__ R Tc[BOX_NB_MAX + 1][CH], Ts[BOX_NB_MAX + 1][CH];
+  __shared__ cx<R> TW[BOX_NB_MAX][CH];  // (cos, sin)(2 pi q o / P) for the general input slots
   const int nb = g.nb[ax], P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
@@ -238,82 +222,52 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   const bool realx = ax == 0 && pxf < P;
   const int o0 = chunk * CH;
   const int no = min(CH, nb - o0);
-  for (int i = threadIdx.x; i < (half + 1) * CH; i += NT) {
+  for (int i = threadIdx.x; i < half * CH; i += NT) {
     const int q = i / CH, c = i % CH;
     const int n = (int)(((int64_t)q * (o0 + c)) % P);
-    Tc[q][c] = tw.w[n].re;
-    Ts[q][c] = -tw.w[n].im;
+    TW[q][c] = cx<R>{tw.w[n].re, -tw.w[n].im};
   }
-  const int m0 = blockIdx.x * (NT * CELLS) + threadIdx.x;
+  const int m = blockIdx.x * NT + threadIdx.x;
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   const int gbase = l1 * (a1 == 0 ? 1 : g.nb[0]) + l2 * (a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
-  const cx<R> *src = in + field * fstride + lbase;
-  // input slot q: X_q and (1 <= q < P/2) X_{P-q}, the latter conj(X_q) for a real field
-  auto fetch = [&](int q, cx<R>(&xa)[CELLS], cx<R>(&xb)[CELLS]) {
-#pragma unroll
-    for (int c = 0; c < CELLS; ++c) {
-      xa[c] = src[q * bsa + m0 + NT * c];
-      if (q != 0 && q != half) xb[c] = realx ? conj(xa[c]) : src[(P - q) * bsa + m0 + NT * c];
-    }
+  const cx<R> *src = in + field * fstride + lbase + m;
+  // general input slot q (1 <= q < half): X_q and X_{P-q}, the latter conj(X_q) for a real field
+  auto fetch = [&](int q, cx<R> &xa, cx<R> &xb) {
+    xa = src[q * bsa];
+    xb = realx ? conj(xa) : src[(P - q) * bsa];
   };
   __syncthreads();
-  cx<R> y[CELLS][CH];
+  // slots 0 and half: coefficients 1 and (-1)^o
+  const cx<R> X0 = src[0], Xh = src[half * bsa];
+  cx<R> y[CH];
 #pragma unroll
-  for (int c = 0; c < CELLS; ++c)
-#pragma unroll
-    for (int k = 0; k < CH; ++k) y[c][k] = cx_zero<R>();
-  cx<R> na[CELLS], nbv[CELLS];
-  fetch(0, na, nbv);
-  for (int q = 0; q <= half; ++q) {
-    cx<R> xa[CELLS], xb[CELLS];
-#pragma unroll
-    for (int c = 0; c < CELLS; ++c) {
-      xa[c] = na[c];
-      xb[c] = nbv[c];
-    }
-    if (q < half) fetch(q + 1, na, nbv);
-    if (q == 0 || q == half) {
-#pragma unroll
-      for (int k = 0; k < CH; ++k) {
-        if (k >= no) break;
-        const bool neg = q == half && ((o0 + k) & 1);
-#pragma unroll
-        for (int c = 0; c < CELLS; ++c) y[c][k] = neg ? csub(y[c][k], xa[c]) : cadd(y[c][k], xa[c]);
-      }
-      continue;
-    }
-    cx<R> U[CELLS], V[CELLS];
-#pragma unroll
-    for (int c = 0; c < CELLS; ++c) {
-      U[c] = cadd(xa[c], xb[c]);
-      V[c] = csub(xa[c], xb[c]);
-    }
+  for (int k = 0; k < CH; ++k) y[k] = ((o0 + k) & 1) ? csub(X0, Xh) : cadd(X0, Xh);
+  cx<R> na = cx_zero<R>(), nbv = cx_zero<R>();
+  if (half > 1) fetch(1, na, nbv);
+  for (int q = 1; q < half; ++q) {
+    const cx<R> xa = na, xb = nbv;
+    if (q + 1 < half) fetch(q + 1, na, nbv);
+    const cx<R> U = cadd(xa, xb), V = csub(xa, xb);
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
-      if (k >= no) break;
-      if (o0 + k == 0) {
-#pragma unroll
-        for (int c = 0; c < CELLS; ++c) y[c][k] = cadd(y[c][k], U[c]);
-        continue;
-      }
-      const R cc = Tc[q][k], ss = Ts[q][k];
-#pragma unroll
-      for (int c = 0; c < CELLS; ++c) {
-        y[c][k].re = rdot2(y[c][k].re, cc, U[c].re, ss, V[c].im, -1.0f);
-        if (!realx) y[c][k].im = rdot2(y[c][k].im, cc, U[c].im, ss, V[c].re, 1.0f);
+      if (k < no) {
+        if (o0 + k == 0) {
+          y[k] = cadd(y[k], U);
+        } else {
+          const cx<R> w = TW[q][k];
+          y[k].re = rdot2(y[k].re, w.re, U.re, w.im, V.im, -1.0f);
+          if (!realx) y[k].im = rdot2(y[k].im, w.re, U.im, w.im, V.re, 1.0f);
+        }
       }
     }
   }
   if (!final) {
-    cx<R> *dst = out + field * fstride + lbase;
+    cx<R> *dst = out + field * fstride + lbase + m;
 #pragma unroll
-    for (int k = 0; k < CH; ++k) {
-      if (k >= no) break;
-#pragma unroll
-      for (int c = 0; c < CELLS; ++c) dst[(o0 + k) * bsa + m0 + NT * c] = cnorm(y[c][k]);
-    }
+    for (int k = 0; k < CH; ++k)
+      if (k < no) dst[(o0 + k) * bsa] = cnorm(y[k]);
     return;
   }
   OutSpec<R> ore{}, oim{};
@@ -326,14 +280,11 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   const R sc = RT<R>::from(scale);
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
-    if (k >= no) break;
+    if (k >= no) continue;
     const int bidx = gbase + (o0 + k) * gsa;
-#pragma unroll
-    for (int c = 0; c < CELLS; ++c) {
-      const cx<R> v = cnorm(y[c][k]);
-      box_store<R>(ore, bidx, m0 + NT * c, B3, v.re * sc);
-      if (!realx) box_store<R>(oim, bidx, m0 + NT * c, B3, v.im * sc);
-    }
+    const cx<R> v = cnorm(y[k]);
+    box_store<R>(ore, bidx, m, B3, v.re * sc);
+    if (!realx) box_store<R>(oim, bidx, m, B3, v.im * sc);
   }
 }
 

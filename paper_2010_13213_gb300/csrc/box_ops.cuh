@@ -174,14 +174,14 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
       return;
     }
     // one cell per thread: more resident warps to cover the loads (the passes are latency-bound)
-    constexpr int NT = 128;
+    constexpr int NT = 128, CHF = 4, CHI = 8;
     if (!inverse) {
-      const int nch = (nb_ax + 1 + 3) / 4;  // conjugate pair slots q = 0 .. P/2, four per chunk
-      k_bdft_fwd<R, B, 4, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+      const int nch = std::max(1, (nb_ax - 1 + CHF - 1) / CHF);  // general slots q = 1 .. nb - 1
+      k_bdft_fwd<R, B, CHF, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
           in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, nch, sp);
     } else {
-      const int nch = (nout + 7) / 8;
-      k_bdft_inv<R, B, 8, 1, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+      const int nch = (nout + CHI - 1) / CHI;
+      k_bdft_inv<R, B, CHI, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
           in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, nch, outs, sc);
     }
   };
