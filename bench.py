@@ -160,7 +160,7 @@ def df_box_instructions(B, nb, ncomp):
 
 # DRAM bytes (read + write) of one k_box_mid<df,16> launch on this workload, from one ncu capture of
 # the current kernel (set to None when the kernel changes)
-MID_DF16_TRAFFIC = None
+MID_DF16_TRAFFIC = 125.173504e6 + 33.693184e6
 
 
 def _alu_entry(kern, inst, ms, launches, traffic=None):
@@ -225,6 +225,51 @@ def run_reference(args):
                              "threads_used": oracle.num_threads()},
             "e2e": {"value": val, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_line(L, torch, dev, steps, warmup):
+    """Batched RK3 stage (config 5): 64 uneven ring instances (1-3 levels, finest boxes 32..192 cells),
+    each stage one Poisson solve and one integrating-factor apply per instance in DF32, three chained
+    stages captured in one CUDA graph.  value = Poisson target cells of all instances per stage / stage time
+    (inputs ~1.7 GB, larger than L2, so no flush)."""
+    import lgf_synth as S
+    params = S.batch_instances(64, B=16)
+    inst = [S.ring_instance(p, B=16, n_ext=16) for p in params]
+    table = L.lgf_table_create(16, (14, 14, 14), L.LGF_TBL_BOX_ONLY)
+    meshes = [L.Mesh(mh["levels"], 16, mh["h0"], n_ext=16) for mh, _, _ in inst]
+    fs = [torch.from_numpy(np.concatenate(f, axis=1)).to(dev) for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    gs = [torch.zeros_like(f) for f in fs]
+    tmps = [torch.zeros_like(f) for f in fs]
+    cells = 0
+    for mh, _, _ in inst:
+        n = [len(b) for b in mh["levels"]] + [0]
+        cells += sum((n[k] - n[k + 1] // 8) * 16 ** 3 for k in range(len(n) - 1))
+    b = L.Batch(table, meshes, 3, L.LGF_F64, alpha=[0.1] * 64, opts=L.make_opts(precision=L.LGF_PREC_DF32),
+                nstreams=8)
+    bs = torch.cuda.Stream(dev)  # graph capture needs a stream other than the legacy default one
+    stream = bs.cuda_stream
+    torch.cuda.synchronize()
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    b.graph_create(3, ptr(fs), ptr(phis), ptr(gs), ptr(tmps), stream)
+    for _ in range(max(1, warmup)):
+        b.graph_launch(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bs)
+    for _ in range(steps):
+        b.graph_launch(stream)
+    e1.record(bs)
+    torch.cuda.synchronize()
+    ms_stage = e0.elapsed_time(e1) / (3 * steps)
+    out = {"workload": "64 ring instances, R ~ U[0.5,1.5], sigma/R ~ U[0.1,0.25], 1-3 levels, 16^3 blocks, "
+                       "3 components, alpha = 0.1", "instances": 64, "blocks": int(sum(m.total_blocks for m in meshes)),
+           "target_cells_per_stage": int(cells), "graph_nodes": int(b.graph_nodes()), "stages_per_graph": 3,
+           "ms_per_stage": ms_stage, "value": cells / (ms_stage * 1e-3) / 1e6, "unit": "Mcells/s",
+           "dtype": "df32", "note": "each stage: Poisson solve + heat-kernel apply per instance"}
+    b.close()
+    L.lgf_table_destroy(table)
+    return out
 
 
 def run_gpu(args):
@@ -337,6 +382,7 @@ def run_gpu(args):
         dist.all_reduce(vals, op=dist.ReduceOp.MAX)
     ms_df, ms_64, e2e_ms = vals.tolist()
     L.lgf_table_destroy(table)
+    batch = batch_line(L, torch, dev, 5, 2) if args.batch else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -374,6 +420,7 @@ def run_gpu(args):
                          "threads_used": oracle.num_threads()},
         "e2e": {"value": cells * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s",
                 "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)},
+        "batch_rk3_stage": batch,
         "gpu_launches": int(rep_df.kernel_launches) * args.steps,
         "clocks": clocks,
         "wall_s_timed": {"df32": wall_df, "fp64": wall_64, "fp32": wall_32},
@@ -390,6 +437,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "pair", "box"])
+    ap.add_argument("--batch", default=1, type=int, help="also time the 64-instance batched RK3 stage (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

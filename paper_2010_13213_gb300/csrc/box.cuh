@@ -99,12 +99,12 @@ LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
 // so every multiply has a real coefficient: half the work of the complex products.  k = 0 and k = P/2
 // (coefficients 1 and (-1)^j) are sums.  A real field keeps K1x in [0, P/2] (Hermitian half): its
 // forward x pass stores X_k only and its inverse x pass takes X_{P-k} = conj(X_k) (real output).
-// A thread owns CELLS cells (m, m + NT, ...) and a chunk of CH pair slots (forward) or outputs (inverse);
-// grid = (B^3 / (NT CELLS), lines, field * nchunk + chunk).  The chunk's (c, s) sit in a shared table;
+// A CTA of NT threads owns REP groups of NT consecutive cells (taken one after the other) and a chunk of
+// CH pair slots (forward) or outputs (inverse); grid = (B^3 / (NT REP), lines, field * nchunk + chunk).  The chunk's (c, s) sit in a shared table;
 // the next input is fetched while the current one multiplies.  The first forward pass (gather) reads
 // through the field's input specs, the last inverse pass (final) writes through its output specs.
 // Field f's arrays start at in + f * fstride, out + f * fstride.
-template <class R, int B, int CH, int NT>
+template <class R, int B, int CH, int NT, int REP>
 __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
                                                  int gather, int nchunk, FwdSpecs sp) {
@@ -124,10 +124,9 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   const bool ends = chunk == 0;
   for (int i = threadIdx.x; i < nb * CH; i += NT) {
     const int j = i / CH, c = i % CH;
-    const int n = (int)(((int64_t)j * (q0 + c)) % P);
+    const int n = (j * (q0 + c)) % P;  // < 32 * 32: 32-bit
     TW[j][c] = cx<R>{tw.w[n].re, -tw.w[n].im};
   }
-  const int m = blockIdx.x * NT + threadIdx.x;
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
@@ -145,6 +144,12 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
       }
   }
   const cx<R> *src = in + field * fstride + lbase;
+  cx<R> *dst = out + field * fstride + lbase;
+  __syncthreads();
+  // REP groups of NT consecutive cells per CTA, one after the other (the table serves them all)
+#pragma unroll 1
+  for (int rep = 0; rep < REP; ++rep) {
+  const int m = (blockIdx.x * REP + rep) * NT + threadIdx.x;
   auto fetch = [&](int j) -> cx<R> {
     if (!gather) return src[j * bsa + m];
     const int bidx = gbase + j * gsa;
@@ -163,7 +168,6 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
     if (ns > 2) add(s2);
     return cx<R>{re, im};
   };
-  __syncthreads();
   // j = 0: every coefficient is 1
   cx<R> x = fetch(0);
   cx<R> xn = nb > 1 ? fetch(1) : cx_zero<R>();
@@ -190,7 +194,6 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
       }
     }
   }
-  cx<R> *dst = out + field * fstride + lbase;
   if (ends) {
     dst[m] = cnorm(S0);
     dst[half * bsa + m] = cnorm(Sh);
@@ -204,9 +207,10 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
       if (!realx) dst[(P - q) * bsa + m] = cx<R>{rnorm(a.re - b.im), rnorm(a.im + b.re)};
     }
   }
+  }
 }
 
-template <class R, int B, int CH, int NT>
+template <class R, int B, int CH, int NT, int REP>
 __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
                                                  int final, int nchunk, InvOuts<R> outs, double scale) {
@@ -224,21 +228,34 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   const int no = min(CH, nb - o0);
   for (int i = threadIdx.x; i < half * CH; i += NT) {
     const int q = i / CH, c = i % CH;
-    const int n = (int)(((int64_t)q * (o0 + c)) % P);
+    const int n = (q * (o0 + c)) % P;  // < 32 * 32: 32-bit
     TW[q][c] = cx<R>{tw.w[n].re, -tw.w[n].im};
   }
-  const int m = blockIdx.x * NT + threadIdx.x;
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   const int gbase = l1 * (a1 == 0 ? 1 : g.nb[0]) + l2 * (a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
+  OutSpec<R> ore{}, oim{};
+  if (final) {
+#pragma unroll
+    for (int f = 0; f < BOX_MAXF; ++f)
+      if (f == field) {
+        ore = outs.re[f];
+        oim = outs.im[f];
+      }
+  }
+  const R sc = RT<R>::from(scale);
+  __syncthreads();
+  // REP groups of NT consecutive cells per CTA, one after the other (the table serves them all)
+#pragma unroll 1
+  for (int rep = 0; rep < REP; ++rep) {
+  const int m = (blockIdx.x * REP + rep) * NT + threadIdx.x;
   const cx<R> *src = in + field * fstride + lbase + m;
   // general input slot q (1 <= q < half): X_q and X_{P-q}, the latter conj(X_q) for a real field
   auto fetch = [&](int q, cx<R> &xa, cx<R> &xb) {
     xa = src[q * bsa];
     xb = realx ? conj(xa) : src[(P - q) * bsa];
   };
-  __syncthreads();
   // slots 0 and half: coefficients 1 and (-1)^o
   const cx<R> X0 = src[0], Xh = src[half * bsa];
   cx<R> y[CH];
@@ -268,16 +285,8 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
 #pragma unroll
     for (int k = 0; k < CH; ++k)
       if (k < no) dst[(o0 + k) * bsa] = cnorm(y[k]);
-    return;
+    continue;
   }
-  OutSpec<R> ore{}, oim{};
-#pragma unroll
-  for (int f = 0; f < BOX_MAXF; ++f)
-    if (f == field) {
-      ore = outs.re[f];
-      oim = outs.im[f];
-    }
-  const R sc = RT<R>::from(scale);
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
     if (k >= no) continue;
@@ -285,6 +294,7 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
     const cx<R> v = cnorm(y[k]);
     box_store<R>(ore, bidx, m, B3, v.re * sc);
     if (!realx) box_store<R>(oim, bidx, m, B3, v.im * sc);
+  }
   }
 }
 

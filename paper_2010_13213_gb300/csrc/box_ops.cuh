@@ -174,14 +174,14 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
       return;
     }
     // one cell per thread: more resident warps to cover the loads (the passes are latency-bound)
-    constexpr int NT = 128, CHF = 4, CHI = 8;
+    constexpr int NT = 128, CHF = 4, CHI = 8, REP = 1;
     if (!inverse) {
       const int nch = std::max(1, (nb_ax - 1 + CHF - 1) / CHF);  // general slots q = 1 .. nb - 1
-      k_bdft_fwd<R, B, CHF, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+      k_bdft_fwd<R, B, CHF, NT, REP><<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(
           in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, nch, sp);
     } else {
       const int nch = (nout + CHI - 1) / CHI;
-      k_bdft_inv<R, B, CHI, NT><<<dim3(B3 / NT, lines, n * nch), NT, 0, st>>>(
+      k_bdft_inv<R, B, CHI, NT, REP><<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(
           in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, nch, outs, sc);
     }
   };
