@@ -176,7 +176,8 @@ int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void
  *                  pool is used.
  *   alpha_finest : kappa*dt/h_finest^2 >= 0.
  *   f_dev, g_dev : as for lgf_poisson_solve; g written on Omega_k.
- * Only opts->precision (FP64 or FP32; DF32 runs as FP64) and opts->timing are read.
+ * Only opts->precision (FP64, FP32 or DF32: the arithmetic of the convolution sums) and opts->timing
+ * are read.
  */
 int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev,
                    void *g_dev, int32_t dtype, double alpha_finest, const lgf_solve_opts *opts,

@@ -135,19 +135,33 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, const int4 *blocks, 
   }
 }
 
+// ------------------------------------------------------------------ coarse Laplacian L_{k-1} psi_{k-1}
+// Every cell of the coarse level's blocks (NaN next to an absent block, as fetch gives); grid (nBL, ncomp).
+template <class R>
+__global__ void __launch_bounds__(256) k_lap(LevelDev L, const int4 *blocks, const R *psi, R *out, int64_t cs) {
+  const int b = blockIdx.x, comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+  const int B3 = B * B * B;
+  const int4 bc = blocks[b];
+  const R inv_h2 = RT<R>::from(1.0 / (L.h * L.h));
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+              z = (bc.z << sh) + (off >> (2 * sh));
+    out[comp * cs + (int64_t)b * B3 + off] = lap7<R>(L, psi, cs, comp, x, y, z, inv_h2);
+  }
+}
+
 // ------------------------------------------------------------------ correction source A_k
-// grid (|SA_k|, ncomp).  A[b] for b = SA[i].  k = 0: A = [OM] fhat.
+// grid (|SA_k|, ncomp).  A[b] for b = SA[i].  k = 0: A = [OM] fhat.  `lpsi` = L_{k-1} psi_{k-1} (k_lap).
 template <class R>
 __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks, const int32_t *SA,
                                                  const void *f_user, int dtype, int64_t ucs, R *A, int64_t cs,
-                                                 const R *c, LevelDev Lc, const R *psi, int64_t pcs,
+                                                 const R *c, LevelDev Lc, const R *lpsi, int64_t pcs,
                                                  int has_coarse) {
   const int b = SA[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
   const int u = L.user_of[b];
   const R inv_h2f = RT<R>::from(1.0 / (L.h * L.h));
-  const R inv_h2c = RT<R>::from(1.0 / (Lc.h * Lc.h));
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     const uint8_t cm = L.cellmask[(int64_t)b * B3 + off];
     R v = RT<R>::zero();
@@ -155,8 +169,7 @@ __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks,
     if (has_coarse && (cm & 3)) {
       const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
                 z = (bc.z << sh) + (off >> (2 * sh));
-      const R plp = interp_at<R>(
-          x, y, z, [&](int i, int j, int k) { return lap7<R>(Lc, psi, pcs, comp, i, j, k, inv_h2c); });
+      const R plp = interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, lpsi, pcs, comp, i, j, k); });
       const R lpc = lap7<R>(L, c, cs, comp, x, y, z, inv_h2f);
       v = v + (plp - lpc);
     }
@@ -250,26 +263,54 @@ __global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *bloc
 }
 
 // One separable pass of E_alpha along `axis` over the heat block set; absent neighbours read 0.
+// When the kernel radius fits in a block (r <= B) every tap reads this block or one of its two
+// neighbours along the axis, looked up once per CTA; wider kernels look each cell up in the block map.
+// Sums run unnormalised in double-float (renormalised once per cell).
 template <class R>
 __global__ void __launch_bounds__(256) k_heat_pass(LevelDev L, const int4 *blocks, const int32_t *HB, int axis,
                                                    const R *in, R *out, int64_t cs, HeatW w) {
+  __shared__ R wt[65];
   const int b = HB[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
+  for (int d = threadIdx.x; d <= w.r; d += blockDim.x) wt[d] = RT<R>::from(w.w[d]);
+  __syncthreads();
+  const R *src = in + comp * cs;
+  if (w.r <= B) {
+    const int ex = axis == 0, ey = axis == 1, ez = axis == 2;
+    const int nbm = level_block(L, bc.x - ex, bc.y - ey, bc.z - ez);
+    const int nbp = level_block(L, bc.x + ex, bc.y + ey, bc.z + ez);
+    const int st = 1 << (axis * sh);  // element stride along the axis inside a block
+    for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+      const int la = (off >> (axis * sh)) & (B - 1);
+      const int64_t own = (int64_t)b * B3 + off;
+      R acc = wt[0] * src[own];
+      for (int d = 1; d <= w.r; ++d) {
+        const int lp = la + d, lm = la - d;
+        R s = RT<R>::zero();
+        if (lp < B) s = src[own + d * st];
+        else if (nbp >= 0) s = src[(int64_t)nbp * B3 + off + (lp - B - la) * st];
+        if (lm >= 0) s = radd(s, src[own - d * st]);
+        else if (nbm >= 0) s = radd(s, src[(int64_t)nbm * B3 + off + (lm + B - la) * st]);
+        acc = rfma(acc, wt[d], s);
+      }
+      out[comp * cs + own] = rnorm(acc);
+    }
+    return;
+  }
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
               z = (bc.z << sh) + (off >> (2 * sh));
-    R acc = RT<R>::from(w.w[0]) * in[comp * cs + (int64_t)b * B3 + off];
+    R acc = wt[0] * src[(int64_t)b * B3 + off];
     for (int d = 1; d <= w.r; ++d) {
-      const R wd = RT<R>::from(w.w[d]);
       int blk, o2;
       R s = RT<R>::zero();
       const int dx = axis == 0 ? d : 0, dy = axis == 1 ? d : 0, dz = axis == 2 ? d : 0;
-      if (level_cell(L, x + dx, y + dy, z + dz, blk, o2)) s = s + in[comp * cs + (int64_t)blk * B3 + o2];
-      if (level_cell(L, x - dx, y - dy, z - dz, blk, o2)) s = s + in[comp * cs + (int64_t)blk * B3 + o2];
-      acc = acc + wd * s;
+      if (level_cell(L, x + dx, y + dy, z + dz, blk, o2)) s = src[(int64_t)blk * B3 + o2];
+      if (level_cell(L, x - dx, y - dy, z - dz, blk, o2)) s = radd(s, src[(int64_t)blk * B3 + o2]);
+      acc = rfma(acc, wt[d], s);
     }
-    out[comp * cs + (int64_t)b * B3 + off] = acc;
+    out[comp * cs + (int64_t)b * B3 + off] = rnorm(acc);
   }
 }
 

@@ -234,6 +234,9 @@ LGF_D double rdot2(double acc, double a, double b, double c, double d, float sgn
 }
 LGF_D float rdot2(float acc, float a, float b, float c, float d, float sgn) { return fmaf(a, b, fmaf(sgn * c, d, acc)); }
 LGF_D df rdot2(df acc, df a, df b, df c, df d, float sgn) { return df_dot2_acc_lazy(acc, a, b, c, d, sgn); }
+LGF_D double radd(double a, double b) { return a + b; }
+LGF_D float radd(float a, float b) { return a + b; }
+LGF_D df radd(df a, df b) { return df_add_lazy(a, b); }
 template <class R>
 LGF_D R rnorm(R a) { return a; }
 template <>

@@ -187,11 +187,12 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       (rc = ws->buf[3].reserve(sizeof(cx<R>) * (size_t)ncomp * std::max<int64_t>(maxSB, 1) * W)) ||
       (rc = ws->buf[4].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[5].reserve(field)) ||
       (rc = ws->buf[6].reserve(field)) || (rc = ws->buf[7].reserve(sizeof(R) * (size_t)Foff[K])) ||
-      (rc = ws->buf[9].reserve(sizeof(unsigned long long) * 2 * K)))
+      (rc = ws->buf[9].reserve(sizeof(unsigned long long) * 2 * K)) || (rc = ws->buf[8].reserve(field)))
     return rc;
   cx<R> *FA = (cx<R> *)ws->buf[0].p, *Phi = (cx<R> *)ws->buf[1].p, *FB = (cx<R> *)ws->buf[3].p;
   R *Fall = (R *)ws->buf[4].p, *A = (R *)ws->buf[5].p, *c = (R *)ws->buf[6].p;
   R *Psi = (R *)ws->buf[7].p;  // psi_k of every level, [level][ncomp][nBL_k][B^3]
+  R *Lpsi = (R *)ws->buf[8].p;  // L_{k-1} psi_{k-1} of the current coarse level
   unsigned long long *racc = (unsigned long long *)ws->buf[9].p;
   int64_t launches = 0;
   PhaseTimer tm;
@@ -228,8 +229,13 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       tm.mark(PH_INTERP);
     }
     if (nSA) {
+      if (k > 0) {  // L_{k-1} psi_{k-1} once per coarse cell, then interpolated per fine cell
+        k_lap<R><<<dim3((unsigned)P->L[k - 1].BL.size(), ncomp), 256, 0, st>>>(Lc, P->L[k - 1].d_BL, psi_prev, Lpsi,
+                                                                               ccs);
+        LGF_LAUNCH_CHECK("coarse Laplacian");
+      }
       k_correct<R><<<dim3(nSA, ncomp), 256, 0, st>>>(Ld, L.d_BL, lists + L.off_SA, f, dtype, ucs, A, cs[k], c, Lc,
-                                                     psi_prev, ccs, k > 0);
+                                                     Lpsi, ccs, k > 0);
       LGF_LAUNCH_CHECK("correct");
       tm.mark(PH_CORRECT);
     }
@@ -531,6 +537,7 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
 int solve_heat(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype, double alpha,
                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
   if (o.precision == LGF_PREC_FP32) return heat_t<float>(t, m, ncomp, f, g, dtype, alpha, o, rep, st);
+  if (o.precision == LGF_PREC_DF32) return heat_t<df>(t, m, ncomp, f, g, dtype, alpha, o, rep, st);
   return heat_t<double>(t, m, ncomp, f, g, dtype, alpha, o, rep, st);
 }
 
