@@ -281,18 +281,23 @@ __global__ void __launch_bounds__(256) k_heat_pass(LevelDev L, const int4 *block
     const int nbm = level_block(L, bc.x - ex, bc.y - ey, bc.z - ez);
     const int nbp = level_block(L, bc.x + ex, bc.y + ey, bc.z + ez);
     const int st = 1 << (axis * sh);  // element stride along the axis inside a block
+    // tap d reads element la + d (la - d) of this line: this block, or the neighbour at local la + d - B
+    // (la - d + B); a missing neighbour contributes 0.  Addresses are selected, not branched, and four
+    // taps are unrolled so their loads are in flight together.
+    const int64_t bp = nbp >= 0 ? (int64_t)(nbp - b) * B3 - (int64_t)B * st : 0;  // + own + d st
+    const int64_t bm = nbm >= 0 ? (int64_t)(nbm - b) * B3 + (int64_t)B * st : 0;  // + own - d st
     for (int off = threadIdx.x; off < B3; off += blockDim.x) {
       const int la = (off >> (axis * sh)) & (B - 1);
       const int64_t own = (int64_t)b * B3 + off;
       R acc = wt[0] * src[own];
+#pragma unroll 4
       for (int d = 1; d <= w.r; ++d) {
-        const int lp = la + d, lm = la - d;
-        R s = RT<R>::zero();
-        if (lp < B) s = src[own + d * st];
-        else if (nbp >= 0) s = src[(int64_t)nbp * B3 + off + (lp - B - la) * st];
-        if (lm >= 0) s = radd(s, src[own - d * st]);
-        else if (nbm >= 0) s = radd(s, src[(int64_t)nbm * B3 + off + (lm + B - la) * st]);
-        acc = rfma(acc, wt[d], s);
+        const bool inp = la + d < B, inm = la - d >= 0;
+        const bool okp = inp || nbp >= 0, okm = inm || nbm >= 0;
+        const int64_t ip = own + d * st + (inp ? 0 : bp), im = own - d * st + (inm ? 0 : bm);
+        const R vp = okp ? src[ip] : RT<R>::zero();
+        const R vm = okm ? src[im] : RT<R>::zero();
+        acc = rfma(acc, wt[d], radd(vp, vm));
       }
       out[comp * cs + own] = rnorm(acc);
     }
