@@ -438,12 +438,31 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "pair", "box"])
     ap.add_argument("--batch", default=1, type=int, help="also time the 64-instance batched RK3 stage (0: skip)")
+    ap.add_argument("--workload", default="ring", choices=["ring", "batch"],
+                    help="batch: only the 64-instance batched RK3 stage (its own JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_only(args)
     else:
         run_gpu(args)
+
+
+def run_batch_only(args):
+    """The batched RK3 stage alone (one replica per rank), printed by rank 0."""
+    import torch
+    import paper_2010_13213_gb300.lgf as L
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    out = batch_line(L, torch, torch.device("cuda", local), args.steps, args.warmup)
+    if rank == 0:
+        line = {"metric": "batched RK3 stage, Poisson target Mcells/s", "value": out["value"] * world,
+                "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": out["ms_per_stage"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "df32", "data": "synthetic", "config": out}
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
