@@ -143,7 +143,7 @@ def df_box_instructions(B, nb, ncomp):
     twiddled = sum(sum(1 for j in range(1, ln // 2) if j * (64 // ln) != 16) * (B // ln)
                    for ln in [2 ** s for s in range(1, lg + 1)])
     fft1d = twiddled * CMUL + (B // 2) * lg * 2 * CADD + B * CNORM
-    mid_block = 6 * B * B * fft1d + 2 * B3 * 2 * CMUL + B3 * 2 * DFMUL
+    mid_block = 6 * B * B * fft1d + 2 * B3 * CMUL + B3 * 2 * DFMUL  # one twiddle product per cell each way
     dft = mid = 0
     fields = [px] * (ncomp // 2) + [px // 2 + 1] * (ncomp % 2)
     for pxu in fields:
@@ -160,7 +160,7 @@ def df_box_instructions(B, nb, ncomp):
 
 # DRAM bytes (read + write) of one k_box_mid<df,16> launch on this workload, from one ncu capture of
 # the current kernel (set to None when the kernel changes)
-MID_DF16_TRAFFIC = 125.173504e6 + 33.693184e6
+MID_DF16_TRAFFIC = None
 
 
 def _alu_entry(kern, inst, ms, launches, traffic=None):

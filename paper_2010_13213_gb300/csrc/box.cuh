@@ -351,7 +351,8 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
 // instruction-cache stalls).  Four barriers, one shared store and load per cell and step.  Ghat is stored
 // per block as [x][z][y] so the x lines of step 2 read it coalesced.  Shared memory: B^3 complex with
 // rows padded to B + 1 (every line direction conflict-free).  Without MULTIPLY (kernel-spectrum
-// generation) the real part of step 2 goes to `kout` in the same [x][z][y] order.
+// generation) the real part of step 2 goes to `kout` in the same [x][z][y] order.  The per-cell twiddle
+// is one load from a table of W_L^n, L = lcm of the three lattice periods, at an integer exponent.
 template <int B>
 struct MidGeom {
   static constexpr int RS = B + 1;          // padded row
@@ -361,31 +362,29 @@ struct MidGeom {
 template <class R, int B, bool MULTIPLY>
 __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64_t fstride,
                                                     const R *__restrict__ Gh, BoxGeom g,
-                                                    const cx<R> *__restrict__ twx, const cx<R> *__restrict__ twy,
-                                                    const cx<R> *__restrict__ twz, Tw64<R> tw,
+                                                    const cx<R> *__restrict__ twl, int L, int3 twf, Tw64<R> tw,
                                                     R *__restrict__ kout) {
   constexpr int B2 = B * B, B3 = B * B * B, RS = B + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
-  __shared__ cx<R> T[3][B];
   // K1 block: blockIdx.x runs over K1x < the launch's widest range; a real field stops at Px/2
   const int pxm = box_pxmax(g);
   const int k1x = (int)(blockIdx.x % pxm), k1y = (int)((blockIdx.x / pxm) % g.P[1]);
   const int k1z = (int)(blockIdx.x / ((unsigned)pxm * g.P[1]));
   if (k1x >= box_pxu(g, blockIdx.y)) return;
   const int64_t kb = k1x + (int64_t)g.P[0] * (k1y + (int64_t)g.P[1] * k1z);  // linear in the full P array
-  const int Pcx = g.P[0] * B, Pcy = g.P[1] * B, Pcz = g.P[2] * B;
-  if (threadIdx.x < 3 * B) {
-    const int a = threadIdx.x / B, mm = threadIdx.x % B;
-    const int k1 = a == 0 ? k1x : (a == 1 ? k1y : k1z);
-    const int Pc = a == 0 ? Pcx : (a == 1 ? Pcy : Pcz);
-    const cx<R> *tab = a == 0 ? twx : (a == 1 ? twy : twz);
-    T[a][mm] = tab[(int)(((int64_t)mm * k1) % Pc)];
-  }
-  __syncthreads();
   cx<R> *Yb = Y + blockIdx.y * fstride + kb * B3;  // field blockIdx.y
   const int t = threadIdx.x, l0 = t % B, l1 = t / B;
-  const cx<R> txy = cmul(T[0][l0], T[1][l1]);  // twiddle of the z line (x, y) = (l0, l1) without z
+  // twiddle W_Pc^{m.K1} of the cell (x, y, z) = (l0, l1, i) of this z line: W_L^{e0 + i ez mod L} with
+  // L = lcm(Pcx, Pcy, Pcz) (m_a K1_a < Pc_a, so each term below is below L: 32-bit)
+  // (kept in shared memory between the first and the last step: no registers held across the FFTs)
+  __shared__ int s_e0[256];
+  __shared__ int s_ez;
+  {
+    const int e0 = (l0 * k1x * twf.x + l1 * k1y * twf.y) % L;
+    s_e0[t] = e0;
+    if (t == 0) s_ez = (k1z * twf.z) % L;
+  }
   cx<R> v[B];
   const int nstep = MULTIPLY ? 6 : 3;
   for (int step = 0; step < nstep; ++step) {
@@ -395,8 +394,14 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
     else if (ax == 1) base = l1 * B * RS + l0, stride = RS;         // y lines: (x, z) = (l0, l1)
     else base = l1 * RS + l0, stride = B * RS;                      // z lines: (x, y) = (l0, l1)
     if (step == 0) {
+      const int ez = (k1z * twf.z) % L;
+      int e = s_e0[t];
 #pragma unroll
-      for (int i = 0; i < B; ++i) v[i] = cmul(Yb[(i * B + l1) * B + l0], cmul(txy, T[2][i]));
+      for (int i = 0; i < B; ++i) {
+        v[i] = cmul(Yb[(i * B + l1) * B + l0], twl[e]);
+        e += ez;
+        if (e >= L) e -= L;
+      }
     } else if (step != 3) {
 #pragma unroll
       for (int i = 0; i < B; ++i) v[i] = S[base + i * stride];
@@ -416,8 +421,14 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
       continue;
     }
     if (step == 5) {
+      const int ez = s_ez;
+      int e = s_e0[t];
 #pragma unroll
-      for (int i = 0; i < B; ++i) Yb[(i * B + l1) * B + l0] = conj(cmul(v[i], cmul(txy, T[2][i])));
+      for (int i = 0; i < B; ++i) {
+        Yb[(i * B + l1) * B + l0] = conj(cmul(v[i], twl[e]));
+        e += ez;
+        if (e >= L) e -= L;
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < B; ++i) S[base + i * stride] = v[i];

@@ -20,13 +20,13 @@ template <>
 inline const df *spec_of<df>(const BoxSpec *S) { return S->gdf; }
 
 template <class R>
-inline const cx<R> *tw_of(const BoxSpec *S, int a);
+inline const cx<R> *twl_of(const BoxSpec *S);
 template <>
-inline const cx<double> *tw_of<double>(const BoxSpec *S, int a) { return S->tw64[a]; }
+inline const cx<double> *twl_of<double>(const BoxSpec *S) { return S->twl64; }
 template <>
-inline const cx<float> *tw_of<float>(const BoxSpec *S, int a) { return S->tw32[a]; }
+inline const cx<float> *twl_of<float>(const BoxSpec *S) { return S->twl32; }
 template <>
-inline const cx<df> *tw_of<df>(const BoxSpec *S, int a) { return S->twdf[a]; }
+inline const cx<df> *twl_of<df>(const BoxSpec *S) { return S->twldf; }
 
 inline void btw_fill(BoxTw<double> &t, const BoxSpec *S, int a) {
   for (int i = 0; i < 2 * BOX_NB_MAX; ++i) t.w[i] = S->bw64[a][i];
@@ -190,9 +190,9 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
   pass(Y0, Y1, 1, make_int3(pxu, 0, nb[2]), pxu * nb[2], 0, 0, 0, 1.0);
   pass(Y1, Y0, 2, make_int3(pxu, P[1], 0), pxu * P[1], 0, 0, 0, 1.0);
   if (mark) mark(mark_ctx, 2);
-  k_box_mid<R, B, true><<<dim3((unsigned)nmid, n), B * B, sm, st>>>(Y0, fstride, spec_of<R>(S), g, tw_of<R>(S, 0),
-                                                                 tw_of<R>(S, 1), tw_of<R>(S, 2), make_tw64<R>(),
-                                                                 nullptr);
+  k_box_mid<R, B, true><<<dim3((unsigned)nmid, n), B * B, sm, st>>>(
+      Y0, fstride, spec_of<R>(S), g, twl_of<R>(S), S->twL, make_int3(S->twf[0], S->twf[1], S->twf[2]),
+      make_tw64<R>(), nullptr);
   if (mark) mark(mark_ctx, 3);
   pass(Y0, Y1, 2, make_int3(pxu, P[1], 0), pxu * P[1], 1, 0, 0, 1.0);
   pass(Y1, Y0, 1, make_int3(pxu, 0, nb[2]), pxu * nb[2], 1, 0, 0, 1.0);

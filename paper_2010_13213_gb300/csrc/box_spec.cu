@@ -7,6 +7,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <numeric>
 #include <vector>
 
 #include "box.cuh"
@@ -109,11 +110,9 @@ BoxSpec::~BoxSpec() {
   cudaFree(g64);
   cudaFree(g32);
   cudaFree(gdf);
-  for (int a = 0; a < 3; ++a) {
-    cudaFree(tw64[a]);
-    cudaFree(tw32[a]);
-    cudaFree(twdf[a]);
-  }
+  cudaFree(twl64);
+  cudaFree(twl32);
+  cudaFree(twldf);
 }
 
 template <int B>
@@ -154,19 +153,6 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
     for (int i = 0; i < g.P[a]; ++i) w[i] = cx<double>{c[i], -s[i]};
     if (cudaMalloc(&wP[a], sizeof(cx<double>) * g.P[a])) return fail(LGF_E_OOM, "tables");
     cudaMemcpyAsync(wP[a], w.data(), sizeof(cx<double>) * g.P[a], cudaMemcpyHostToDevice, st);
-    const int Pc = g.P[a] * B;
-    twiddles_host(Pc, c, s);
-    if (cudaMalloc(&dc, sizeof(double) * Pc) || cudaMalloc(&ds, sizeof(double) * Pc)) return fail(LGF_E_OOM, "tables");
-    if (cudaMalloc(&S->tw64[a], sizeof(cx<double>) * Pc) || cudaMalloc(&S->tw32[a], sizeof(cx<float>) * Pc) ||
-        cudaMalloc(&S->twdf[a], sizeof(cx<df>) * Pc))
-      return fail(LGF_E_OOM, "tables");
-    cudaMemcpyAsync(dc, c.data(), sizeof(double) * Pc, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(ds, s.data(), sizeof(double) * Pc, cudaMemcpyHostToDevice, st);
-    k_tw_convert<<<(Pc + 127) / 128, 128, 0, st>>>(dc, ds, Pc, S->tw64[a], S->tw32[a], S->twdf[a]);
-    cudaStreamSynchronize(st);
-    cudaFree(dc);
-    cudaFree(ds);
-    dc = ds = nullptr;
     std::vector<double> cb, sb;
     twiddles_host(g.P[a], cb, sb);
     for (int i = 0; i < g.P[a] && i < 32; ++i) {
@@ -176,6 +162,27 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
       S->bwdf[a][i] = cx<df>{df{hr, (float)(cb[i] - (double)hr)}, df{hi, (float)(-sb[i] - (double)hi)}};
     }
   }
+  // four-step twiddle table W_L^n, L = lcm of the three lattice periods Pc = P B
+  {
+    const int Pc[3] = {g.P[0] * B, g.P[1] * B, g.P[2] * B};
+    const int L = std::lcm(std::lcm(Pc[0], Pc[1]), Pc[2]);
+    S->twL = L;
+    for (int a = 0; a < 3; ++a) S->twf[a] = L / Pc[a];
+    std::vector<double> c, s;
+    twiddles_host(L, c, s);
+    if (cudaMalloc(&dc, sizeof(double) * L) || cudaMalloc(&ds, sizeof(double) * L)) return fail(LGF_E_OOM, "tables");
+    if (cudaMalloc(&S->twl64, sizeof(cx<double>) * L) || cudaMalloc(&S->twl32, sizeof(cx<float>) * L) ||
+        cudaMalloc(&S->twldf, sizeof(cx<df>) * L))
+      return fail(LGF_E_OOM, "tables");
+    cudaMemcpyAsync(dc, c.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ds, s.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st);
+    k_tw_convert<<<(L + 127) / 128, 128, 0, st>>>(dc, ds, L, S->twl64, S->twl32, S->twldf);
+    cudaStreamSynchronize(st);
+    cudaFree(dc);
+    cudaFree(ds);
+    dc = ds = nullptr;
+    S->bytes += (size_t)L * (16 + 8 + 16);
+  }
   // dense block-index DFTs of the embedded LGF: x (from G), y, z
   const dim3 blk(256);
   const unsigned gx = (B3 + 255) / 256;
@@ -184,8 +191,8 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
   k_bdft_dense<B><<<dim3(gx, g.P[0] * g.P[1]), blk, 0, st>>>(Y1, Y0, g, 2, wP[2], nullptr, 0);
   const size_t sm = sizeof(cx<double>) * (size_t)B * B * (B + 1);
   cudaFuncSetAttribute(k_box_mid<double, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_box_mid<double, B, false><<<dim3((unsigned)nblk, 1), B * B, sm, st>>>(Y0, 0, nullptr, g, S->tw64[0], S->tw64[1],
-                                                                        S->tw64[2], make_tw64<double>(), S->g64);
+  k_box_mid<double, B, false><<<dim3((unsigned)nblk, 1), B * B, sm, st>>>(
+      Y0, 0, nullptr, g, S->twl64, S->twL, make_int3(S->twf[0], S->twf[1], S->twf[2]), make_tw64<double>(), S->g64);
   k_spec_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S->g64, n, S->g32, S->gdf);
   cudaError_t e = cudaStreamSynchronize(st);
   cudaFree(Y0);

@@ -107,9 +107,13 @@ struct BoxSpec {
   double *g64 = nullptr;  // [P^3 blocks][B^3] real spectrum, FP64
   float *g32 = nullptr;
   df *gdf = nullptr;
-  cx<double> *tw64[3] = {nullptr, nullptr, nullptr};  // W_Pc^n per axis, n < Pc
-  cx<float> *tw32[3] = {nullptr, nullptr, nullptr};
-  cx<df> *twdf[3] = {nullptr, nullptr, nullptr};
+  // four-step twiddles: W_L^n, n < L = lcm(Pcx, Pcy, Pcz) (Pc = P B cells per axis); the twiddle of a
+  // cell m and block frequency K1 is W_L^{(sum_a m_a K1_a L / Pc_a) mod L}
+  cx<double> *twl64 = nullptr;
+  cx<float> *twl32 = nullptr;
+  cx<df> *twldf = nullptr;
+  int twL = 0;
+  int twf[3] = {0, 0, 0};  // L / Pc_a
   cx<double> bw64[3][32];  // W_P^n per axis, n < P (host copies for kernel parameters)
   cx<float> bw32[3][32];
   cx<df> bwdf[3][32];
