@@ -89,6 +89,17 @@ LGF_D void box_store(const OutSpec<R> &o, int bidx, int m, int B3, R v) {
   store_field<R>(o.dst, o.off + (int64_t)ob * B3 + m, o.dtype, v);
 }
 
+// The same with the block indices resolved by the caller: ob = scatter[bidx] (-1: skip), ab = the
+// addend / mask block (aux[bidx], or ob without aux).
+template <class R>
+LGF_D void box_store_at(const OutSpec<R> &o, int ob, int ab, int m, int B3, R v) {
+  if (ob < 0) return;
+  const int64_t a = (int64_t)ab * B3 + m;
+  if (o.add) v = v + o.add[a];
+  if (o.mask && !(o.mask[a] & o.bits)) return;
+  store_field<R>(o.dst, o.off + (int64_t)ob * B3 + m, o.dtype, v);
+}
+
 // ------------------------------------------------------------------ block-index DFTs
 // Pass along axis `ax` for every line (the two other block coordinates within `ext`) and local cell m:
 //   forward  X[.. k ..][m] = sum_{j < nb} W_P^{ j k} x[.. j ..][m],   k < P = 2 nb
@@ -143,6 +154,14 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
         ns = sp.n[f];
       }
   }
+  // the line's source block of every input j and spec (the same for all cells of the CTA)
+  __shared__ int GI[3][BOX_NB_MAX];
+  if (gather)
+    for (int i = threadIdx.x; i < 3 * nb; i += NT) {
+      const int si = i / nb, j = i % nb;
+      const InSpec &q = si == 0 ? s0 : (si == 1 ? s1 : s2);
+      GI[si][j] = si < ns ? q.gather[gbase + j * gsa] : -1;
+    }
   const cx<R> *src = in + field * fstride + lbase;
   cx<R> *dst = out + field * fstride + lbase;
   __syncthreads();
@@ -152,10 +171,9 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   const int m = (blockIdx.x * REP + rep) * NT + threadIdx.x;
   auto fetch = [&](int j) -> cx<R> {
     if (!gather) return src[j * bsa + m];
-    const int bidx = gbase + j * gsa;
     R re = RT<R>::zero(), im = RT<R>::zero();
-    auto add = [&](const InSpec &q) {
-      const int idx = q.gather[bidx];
+    auto add = [&](const InSpec &q, int si) {
+      const int idx = GI[si][j];
       if (idx < 0) return;
       const int64_t e = (int64_t)idx * B3 + m;
       if (q.mask && !(q.mask[e] & q.bits)) return;
@@ -163,9 +181,9 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
       if (q.part) im = im + v;
       else re = re + v;
     };
-    if (ns > 0) add(s0);
-    if (ns > 1) add(s1);
-    if (ns > 2) add(s2);
+    if (ns > 0) add(s0, 0);
+    if (ns > 1) add(s1, 1);
+    if (ns > 2) add(s2, 2);
     return cx<R>{re, im};
   };
   // j = 0: every coefficient is 1
@@ -245,6 +263,20 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
       }
   }
   const R sc = RT<R>::from(scale);
+  // output blocks of the chunk's outputs (the same for all cells of the CTA): scatter and addend / mask
+  __shared__ int SO[2][CH], SX[2][CH];
+  if (final && threadIdx.x < 2 * CH) {
+    const int part = threadIdx.x / CH, k = threadIdx.x % CH;
+    const OutSpec<R> &o = part ? oim : ore;
+    int ob = -1, ab = -1;
+    if (k < no && o.scatter) {
+      const int bidx = gbase + (o0 + k) * gsa;
+      ob = o.scatter[bidx];
+      ab = ob >= 0 ? (o.aux ? o.aux[bidx] : ob) : -1;
+    }
+    SO[part][k] = ob;
+    SX[part][k] = ab;
+  }
   __syncthreads();
   // REP groups of NT consecutive cells per CTA, one after the other (the table serves them all)
 #pragma unroll 1
@@ -290,10 +322,9 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
     if (k >= no) continue;
-    const int bidx = gbase + (o0 + k) * gsa;
     const cx<R> v = cnorm(y[k]);
-    box_store<R>(ore, bidx, m, B3, v.re * sc);
-    if (!realx) box_store<R>(oim, bidx, m, B3, v.im * sc);
+    box_store_at<R>(ore, SO[0][k], SX[0][k], m, B3, v.re * sc);
+    if (!realx) box_store_at<R>(oim, SO[1][k], SX[1][k], m, B3, v.im * sc);
   }
   }
 }
