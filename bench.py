@@ -160,7 +160,7 @@ def df_box_instructions(B, nb, ncomp):
 
 # DRAM bytes (read + write) of one k_box_mid<df,16> launch on this workload, from one ncu capture of
 # the current kernel (set to None when the kernel changes)
-MID_DF16_TRAFFIC = 125.352192e6 + 34.542848e6
+MID_DF16_TRAFFIC = None
 
 
 def _alu_entry(kern, inst, ms, launches, traffic=None):

@@ -157,10 +157,11 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   // the line's source block of every input j and spec (the same for all cells of the CTA)
   __shared__ int GI[3][BOX_NB_MAX];
   if (gather)
-    for (int i = threadIdx.x; i < 3 * nb; i += NT) {
-      const int si = i / nb, j = i % nb;
-      const InSpec &q = si == 0 ? s0 : (si == 1 ? s1 : s2);
-      GI[si][j] = si < ns ? q.gather[gbase + j * gsa] : -1;
+    for (int j = threadIdx.x; j < nb; j += NT) {
+      const int bidx = gbase + j * gsa;
+      GI[0][j] = ns > 0 ? s0.gather[bidx] : -1;
+      GI[1][j] = ns > 1 ? s1.gather[bidx] : -1;
+      GI[2][j] = ns > 2 ? s2.gather[bidx] : -1;
     }
   const cx<R> *src = in + field * fstride + lbase;
   cx<R> *dst = out + field * fstride + lbase;
@@ -265,17 +266,22 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   const R sc = RT<R>::from(scale);
   // output blocks of the chunk's outputs (the same for all cells of the CTA): scatter and addend / mask
   __shared__ int SO[2][CH], SX[2][CH];
-  if (final && threadIdx.x < 2 * CH) {
-    const int part = threadIdx.x / CH, k = threadIdx.x % CH;
-    const OutSpec<R> &o = part ? oim : ore;
+  if (final && threadIdx.x < CH) {
+    const int k = threadIdx.x, bidx = gbase + (o0 + k) * gsa;
     int ob = -1, ab = -1;
-    if (k < no && o.scatter) {
-      const int bidx = gbase + (o0 + k) * gsa;
-      ob = o.scatter[bidx];
-      ab = ob >= 0 ? (o.aux ? o.aux[bidx] : ob) : -1;
+    if (k < no && ore.scatter) {
+      ob = ore.scatter[bidx];
+      ab = ob >= 0 ? (ore.aux ? ore.aux[bidx] : ob) : -1;
     }
-    SO[part][k] = ob;
-    SX[part][k] = ab;
+    SO[0][k] = ob;
+    SX[0][k] = ab;
+    ob = ab = -1;
+    if (k < no && oim.scatter) {
+      ob = oim.scatter[bidx];
+      ab = ob >= 0 ? (oim.aux ? oim.aux[bidx] : ob) : -1;
+    }
+    SO[1][k] = ob;
+    SX[1][k] = ab;
   }
   __syncthreads();
   // REP groups of NT consecutive cells per CTA, one after the other (the table serves them all)
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
       } else {
 #pragma unroll
         for (int i = 0; i < B; ++i) {
-          const R gk = Gh[kb * B3 + i * B2 + t];
+          const R gk = ld_stream(Gh + kb * B3 + i * B2 + t);  // read once per solve
           v[i] = cx<R>{v[i].re * gk, -(v[i].im * gk)};
         }
       }

@@ -300,6 +300,14 @@ LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
   for (int i = 0; i < N; ++i) x[i] = cnorm(x[i]);
 }
 
+// Streaming (evict-first) load of data read once, so it does not displace reused data from L2.
+LGF_D double ld_stream(const double *p) { return __ldcs(p); }
+LGF_D float ld_stream(const float *p) { return __ldcs(p); }
+LGF_D df ld_stream(const df *p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+  return df{v.x, v.y};
+}
+
 // ------------------------------------------------------------------ loads/stores of fields
 // dtype 0: double storage, 1: float storage, 2: the kernel's own arithmetic type R (internal buffers).
 template <class R>
