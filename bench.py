@@ -142,7 +142,7 @@ def df_box_instructions(B, nb, ncomp):
     # radix-2 FFT of B points: twiddled butterflies except W = 1 and W = -i (an exact swap)
     twiddled = sum(sum(1 for j in range(1, ln // 2) if j * (64 // ln) != 16) * (B // ln)
                    for ln in [2 ** s for s in range(1, lg + 1)])
-    fft1d = twiddled * CMUL + (B // 2) * lg * 2 * CADD + B * CNORM
+    fft1d = twiddled * CMUL + (B // 2) * lg * 2 * CADD  # lazily added; no renormalisation between steps
     mid_block = 6 * B * B * fft1d + 2 * B3 * CMUL + B3 * 2 * DFMUL  # one twiddle product per cell each way
     dft = mid = 0
     fields = [px] * (ncomp // 2) + [px // 2 + 1] * (ncomp % 2)

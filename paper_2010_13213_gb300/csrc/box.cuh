@@ -443,7 +443,9 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
 #pragma unroll
       for (int i = 0; i < B; ++i) v[i] = S[base + i * stride];
     }
-    fft_reg<R, B, false>(v, tw);
+    // no renormalisation between the line FFTs: the next step's butterflies add lazily, and the kernel
+    // product and the final twiddle product renormalise
+    fft_reg<R, B, false, false>(v, tw);
     if (step == 2) {
       if (!MULTIPLY) {
 #pragma unroll

@@ -267,8 +267,10 @@ LGF_HD constexpr int bitrev(int i) {
   return r;
 }
 
-// In-register radix-2 decimation-in-time FFT of length N (power of two <= 64), unnormalised.
-template <class R, int N, bool INV>
+// In-register radix-2 decimation-in-time FFT of length N (power of two <= 64), unnormalised.  NORM = false
+// leaves double-float outputs unrenormalised (hi + lo still exact: for callers whose next operations are
+// lazy sums and error-compensated products, which renormalise themselves).
+template <class R, int N, bool INV, bool NORM = true>
 LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -296,8 +298,9 @@ LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
       }
     }
   }
+  if (NORM)
 #pragma unroll
-  for (int i = 0; i < N; ++i) x[i] = cnorm(x[i]);
+    for (int i = 0; i < N; ++i) x[i] = cnorm(x[i]);
 }
 
 // Streaming (evict-first) load of data read once, so it does not displace reused data from L2.
