@@ -396,12 +396,89 @@ struct MidGeom {
   static constexpr int N = B * B * RS;      // padded elements
 };
 
+// Exchange with the lane 16 apart in the warp (the other half of the same line).
+LGF_D double shfl16(double v) { return __shfl_xor_sync(0xffffffffu, v, 16); }
+LGF_D float shfl16(float v) { return __shfl_xor_sync(0xffffffffu, v, 16); }
+LGF_D df shfl16(df v) { return df{__shfl_xor_sync(0xffffffffu, v.hi, 16), __shfl_xor_sync(0xffffffffu, v.lo, 16)}; }
+template <class R>
+LGF_D cx<R> shfl16(cx<R> v) { return cx<R>{shfl16(v.re), shfl16(v.im)}; }
+
+// Line FFT split over two threads: half h holds the points 2r + h (r < H = B/2) and runs the H-point
+// FFT of its half (E: even points, O: odd points); the last radix-2 stage X_k = E_k + W_B^k O_k,
+// X_{k+H} = E_k - W_B^k O_k is shared out by k, half h taking k in [hQ, hQ + Q), Q = B/4, after one
+// exchange of Q values.  Output slot j of half h then holds X at mid_out_index(B, h, j).
+LGF_HD constexpr int mid_out_index(int B, int h, int j) { return h * (B / 4) + j % (B / 4) + (B / 2) * (j / (B / 4)); }
+
+template <class R, int B>
+LGF_D void fft_split(cx<R> (&u)[B / 2], int h, const Tw64<R> &tw) {
+  constexpr int Q = B / 4;
+  fft_reg<R, B / 2, false, false>(u, tw);
+#pragma unroll
+  for (int r = 0; r < Q; ++r) {
+    const cx<R> recv = shfl16(h ? u[r] : u[Q + r]);  // half 0 sends E_{Q+r}, half 1 sends O_r
+    const cx<R> E = h ? recv : u[r], O = h ? u[Q + r] : recv;
+    cx<R> t;
+    if (r == 0) {  // k = 0 (W = 1) or k = B/4 (W = -i, an exact swap)
+      t = h ? cx<R>{O.im, -O.re} : O;
+    } else {
+      const cx<R> w0 = twiddle<R, 64, false>(tw, r * (64 / B)), w1 = twiddle<R, 64, false>(tw, (Q + r) * (64 / B));
+      t = cmul(O, h ? w1 : w0);
+    }
+    u[r] = cadd(E, t);
+    u[Q + r] = csub(E, t);
+  }
+}
+
+// Source of slot r (point 2r + h) of half h when the output of fft_split feeds another split FFT of the
+// same line: >= 0, the half's own slot; < 0, -(s + 1) for the s-th value received from the other half,
+// which sends its slots 2s + h.
+LGF_HD constexpr int mid_regroup_src(int B, int h, int r) {
+  const int m = 2 * r + h, H = B / 2, Q = B / 4;
+  if ((m % H) / Q == h) return (m % H) % Q + Q * (m / H);
+  int src = 0;
+  for (int s = 0; s < H / 2; ++s)
+    if (mid_out_index(B, 1 - h, 2 * s + h) == m) src = -(s + 1);
+  return src;
+}
+
+template <class R, int B>
+LGF_D void mid_regroup(cx<R> (&u)[B / 2], int h) {
+  constexpr int H = B / 2;
+  cx<R> recv[H / 2], nu[H];
+#pragma unroll
+  for (int s = 0; s < H / 2; ++s) recv[s] = shfl16(h ? u[2 * s] : u[2 * s + 1]);
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    const int c0 = mid_regroup_src(B, 0, r), c1 = mid_regroup_src(B, 1, r);
+    const cx<R> v0 = c0 >= 0 ? u[c0 >= 0 ? c0 : 0] : recv[c0 < 0 ? -c0 - 1 : 0];
+    const cx<R> v1 = c1 >= 0 ? u[c1 >= 0 ? c1 : 0] : recv[c1 < 0 ? -c1 - 1 : 0];
+    nu[r] = h ? v1 : v0;
+  }
+#pragma unroll
+  for (int r = 0; r < H; ++r) u[r] = nu[r];
+}
+
+// Lines per thread of k_box_mid: FP32 splits each line over two threads (half the registers per thread,
+// twice the resident warps, one exchange per FFT); double-float and FP64 keep a whole line per thread,
+// where the exchanges (two or four words per complex value) and the register limit of the doubled block
+// cost more than the occupancy gains.
+template <class R>
+struct MidSplit {
+  static constexpr bool value = false;
+};
+template <>
+struct MidSplit<float> {
+  static constexpr bool value = true;
+};
+template <class R, int B>
+constexpr int mid_threads() { return (MidSplit<R>::value ? 2 : 1) * B * B; }
+
 template <class R, int B, bool MULTIPLY>
-__global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64_t fstride,
-                                                    const R *__restrict__ Gh, BoxGeom g,
-                                                    const cx<R> *__restrict__ twl, int L, int3 twf, Tw64<R> tw,
-                                                    R *__restrict__ kout) {
-  constexpr int B2 = B * B, B3 = B * B * B, RS = B + 1;
+__global__ void __launch_bounds__(mid_threads<R, B>(), 512 / (B * B)) k_box_mid(
+    cx<R> *__restrict__ Y, int64_t fstride, const R *__restrict__ Gh, BoxGeom g, const cx<R> *__restrict__ twl,
+    int L, int3 twf, Tw64<R> tw, R *__restrict__ kout) {
+  constexpr bool SPLIT = MidSplit<R>::value;
+  constexpr int B2 = B * B, B3 = B * B * B, RS = B + 1, NV = SPLIT ? B / 2 : B, Q = B / 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R> *S = reinterpret_cast<cx<R> *>(smem_raw);
   // K1 block: blockIdx.x runs over K1x < the launch's widest range; a real field stops at Px/2
@@ -411,18 +488,22 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
   if (k1x >= box_pxu(g, blockIdx.y)) return;
   const int64_t kb = k1x + (int64_t)g.P[0] * (k1y + (int64_t)g.P[1] * k1z);  // linear in the full P array
   cx<R> *Yb = Y + blockIdx.y * fstride + kb * B3;  // field blockIdx.y
-  const int t = threadIdx.x, l0 = t % B, l1 = t / B;
+  // line t = (l0, l1).  SPLIT: lanes 0-15 of warp w hold the even points of the lines 16w .. 16w + 15,
+  // lanes 16-31 the odd points of the same lines (each quarter-warp keeps the one-line-per-lane pattern)
+  const int h = SPLIT ? (threadIdx.x >> 4) & 1 : 0;
+  const int t = SPLIT ? (threadIdx.x >> 5) * 16 + (threadIdx.x & 15) : threadIdx.x, l0 = t % B, l1 = t / B;
+  // point of the line in input slot r / output slot j of this thread
+  auto in_idx = [h](int r) { return SPLIT ? 2 * r + h : r; };
+  auto out_idx = [h](int j) { return SPLIT ? mid_out_index(B, h, j) : j; };
   // twiddle W_Pc^{m.K1} of the cell (x, y, z) = (l0, l1, i) of this z line: W_L^{e0 + i ez mod L} with
   // L = lcm(Pcx, Pcy, Pcz) (m_a K1_a < Pc_a, so each term below is below L: 32-bit)
   // (kept in shared memory between the first and the last step: no registers held across the FFTs)
-  __shared__ int s_e0[256];
+  __shared__ int s_e0[B2];
   __shared__ int s_ez;
-  {
-    const int e0 = (l0 * k1x * twf.x + l1 * k1y * twf.y) % L;
-    s_e0[t] = e0;
-    if (t == 0) s_ez = (k1z * twf.z) % L;
-  }
-  cx<R> v[B];
+  if (h == 0) s_e0[t] = (l0 * k1x * twf.x + l1 * k1y * twf.y) % L;
+  if (threadIdx.x == 0) s_ez = (k1z * twf.z) % L;
+  __syncthreads();
+  cx<R> v[NV];
   const int nstep = MULTIPLY ? 6 : 3;
   for (int step = 0; step < nstep; ++step) {
     const int ax = step < 3 ? 2 - step : step - 3;
@@ -431,46 +512,55 @@ __global__ void __launch_bounds__(256, 2) k_box_mid(cx<R> *__restrict__ Y, int64
     else if (ax == 1) base = l1 * B * RS + l0, stride = RS;         // y lines: (x, z) = (l0, l1)
     else base = l1 * RS + l0, stride = B * RS;                      // z lines: (x, y) = (l0, l1)
     if (step == 0) {
-      const int ez = (k1z * twf.z) % L;
-      int e = s_e0[t];
+      const int ez = s_ez, dez = SPLIT ? (2 * ez) % L : ez;
+      int e = (s_e0[t] + h * ez) % L;
 #pragma unroll
-      for (int i = 0; i < B; ++i) {
-        v[i] = cmul(Yb[(i * B + l1) * B + l0], twl[e]);
-        e += ez;
+      for (int r = 0; r < NV; ++r) {
+        const int i = in_idx(r);
+        v[r] = cmul(Yb[(i * B + l1) * B + l0], twl[e]);
+        e += dez;
         if (e >= L) e -= L;
       }
-    } else if (step != 3) {
+    } else if (step == 3) {
+      if constexpr (SPLIT) mid_regroup<R, B>(v, h);  // the same x lines, in registers
+    } else {
 #pragma unroll
-      for (int i = 0; i < B; ++i) v[i] = S[base + i * stride];
+      for (int r = 0; r < NV; ++r) v[r] = S[base + in_idx(r) * stride];
     }
     // no renormalisation between the line FFTs: the next step's butterflies add lazily, and the kernel
     // product and the final twiddle product renormalise
-    fft_reg<R, B, false, false>(v, tw);
+    if constexpr (SPLIT) fft_split<R, B>(v, h, tw);
+    else fft_reg<R, B, false, false>(v, tw);
     if (step == 2) {
       if (!MULTIPLY) {
 #pragma unroll
-        for (int i = 0; i < B; ++i) kout[kb * B3 + i * B2 + t] = v[i].re;
+        for (int j = 0; j < NV; ++j) kout[kb * B3 + out_idx(j) * B2 + t] = v[j].re;
       } else {
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-          const R gk = ld_stream(Gh + kb * B3 + i * B2 + t);  // read once per solve
-          v[i] = cx<R>{v[i].re * gk, -(v[i].im * gk)};
+        for (int j = 0; j < NV; ++j) {
+          const R gk = ld_stream(Gh + kb * B3 + out_idx(j) * B2 + t);  // read once per solve
+          v[j] = cx<R>{v[j].re * gk, -(v[j].im * gk)};
         }
       }
       continue;
     }
     if (step == 5) {
-      const int ez = s_ez;
-      int e = s_e0[t];
+      const int ez = s_ez, e0 = s_e0[t];
+      int e = 0;
 #pragma unroll
-      for (int i = 0; i < B; ++i) {
-        Yb[(i * B + l1) * B + l0] = conj(cmul(v[i], twl[e]));
-        e += ez;
-        if (e >= L) e -= L;
+      for (int j = 0; j < NV; ++j) {
+        const int i = out_idx(j);
+        if (j == 0 || (SPLIT && j == Q)) {
+          e = (e0 + i * ez) % L;
+        } else {
+          e += ez;
+          if (e >= L) e -= L;
+        }
+        Yb[(i * B + l1) * B + l0] = conj(cmul(v[j], twl[e]));
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < B; ++i) S[base + i * stride] = v[i];
+      for (int j = 0; j < NV; ++j) S[base + out_idx(j) * stride] = v[j];
       __syncthreads();
     }
   }

@@ -190,7 +190,7 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
   pass(Y0, Y1, 1, make_int3(pxu, 0, nb[2]), pxu * nb[2], 0, 0, 0, 1.0);
   pass(Y1, Y0, 2, make_int3(pxu, P[1], 0), pxu * P[1], 0, 0, 0, 1.0);
   if (mark) mark(mark_ctx, 2);
-  k_box_mid<R, B, true><<<dim3((unsigned)nmid, n), B * B, sm, st>>>(
+  k_box_mid<R, B, true><<<dim3((unsigned)nmid, n), mid_threads<R, B>(), sm, st>>>(
       Y0, fstride, spec_of<R>(S), g, twl_of<R>(S), S->twL, make_int3(S->twf[0], S->twf[1], S->twf[2]),
       make_tw64<R>(), nullptr);
   if (mark) mark(mark_ctx, 3);

@@ -191,7 +191,7 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
   k_bdft_dense<B><<<dim3(gx, g.P[0] * g.P[1]), blk, 0, st>>>(Y1, Y0, g, 2, wP[2], nullptr, 0);
   const size_t sm = sizeof(cx<double>) * (size_t)B * B * (B + 1);
   cudaFuncSetAttribute(k_box_mid<double, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_box_mid<double, B, false><<<dim3((unsigned)nblk, 1), B * B, sm, st>>>(
+  k_box_mid<double, B, false><<<dim3((unsigned)nblk, 1), mid_threads<double, B>(), sm, st>>>(
       Y0, 0, nullptr, g, S->twl64, S->twL, make_int3(S->twf[0], S->twf[1], S->twf[2]), make_tw64<double>(), S->g64);
   k_spec_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S->g64, n, S->g32, S->gdf);
   cudaError_t e = cudaStreamSynchronize(st);
