@@ -45,7 +45,7 @@ extern "C" {
 #define LGF_E_CUDA (-5)         /* a CUDA runtime call or kernel launch failed */
 #define LGF_E_TIMEOUT (-6)      /* a bounded device-side wait gave up (batched scheduler) */
 #define LGF_E_PRECISION (-7)    /* FP64 residual above opts->residual_tol */
-#define LGF_E_UNSUPPORTED (-8)  /* valid request this build does not implement */
+#define LGF_E_UNSUPPORTED (-8)  /* valid request the library does not implement */
 
 /* ---- storage types of caller fields */
 #define LGF_F64 0
