@@ -128,3 +128,21 @@ def test_box_three_level_ring_matches_pair(L, tables):
         for c in range(2):
             assert rel(g[c][msk], r[c][msk]) <= 1e-12
             assert rel(a[c][msk], r[c][msk]) <= 1e-10
+
+
+@pytest.mark.parametrize("mode", ["box", "pair"])
+def test_df32_field_conversions_across_exponents(L, tables, mode):
+    """Double-float solves convert the double fields they read and write: scaling the source by 2^k (with
+    exact zeros mixed in) scales the solution by 2^k at the same relative accuracy."""
+    case = S.single_level_random(n=32, B=16, seed=21, ncomp=2)
+    f = case["f"].copy()
+    f[:, :, ::7] = 0.0  # exact zeros among the source cells
+    box = S.blocks_to_box(f, case["blocks"], 16, case["shape"])
+    ref = oracle.solve_box_fft(box, case["h"])
+    mac = L.LGF_MAC_BOX if mode == "box" else L.LGF_MAC_PAIR
+    for k in (-80, -30, 0, 30, 80):
+        s = 2.0 ** k
+        phi = solve(L, tables[16], [case["blocks"]], 16, case["h"], f * s, 2, mac)
+        got = S.blocks_to_box(phi, case["blocks"], 16, case["shape"])
+        for c in range(2):
+            assert rel(got[c], ref[c] * s) <= TOL[2], (k, c, rel(got[c], ref[c] * s))
