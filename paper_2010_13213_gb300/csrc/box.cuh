@@ -196,13 +196,14 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
     A[k] = x;
     Bv[k] = cx_zero<R>();
   }
-  cx<R> S0 = x, Sh = x;  // slot 0 (coefficients 1) and slot half (coefficients (-1)^j)
+  // slots 0 and half (coefficients 1 and (-1)^j) from the sums over even and odd j
+  cx<R> Se = x, So = cx_zero<R>();
   for (int j = 1; j < nb; ++j) {
     x = xn;
     if (j + 1 < nb) xn = fetch(j + 1);
     if (ends) {
-      S0 = cadd(S0, x);
-      Sh = (j & 1) ? csub(Sh, x) : cadd(Sh, x);
+      if (j & 1) So = cadd(So, x);
+      else Se = cadd(Se, x);
     }
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
@@ -214,8 +215,8 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
     }
   }
   if (ends) {
-    dst[m] = cnorm(S0);
-    dst[half * bsa + m] = cnorm(Sh);
+    dst[m] = cnorm(cadd(Se, So));
+    dst[half * bsa + m] = cnorm(csub(Se, So));
   }
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
