@@ -174,7 +174,7 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
       return;
     }
     // one cell per thread: more resident warps to cover the loads (the passes are latency-bound)
-    constexpr int NT = 128, CHF = 5, CHI = 8, REP = 1;
+    constexpr int NT = 128, CHF = 5, CHI = 6, REP = 1;
     if (!inverse) {
       const int nch = std::max(1, (nb_ax - 1 + CHF - 1) / CHF);  // general slots q = 1 .. nb - 1
       k_bdft_fwd<R, B, CHF, NT, REP><<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(
