@@ -115,29 +115,39 @@ LGF_D void box_store_at(const OutSpec<R> &o, int ob, int ab, int m, int B3, R v)
 // the next input is fetched while the current one multiplies.  The first forward pass (gather) reads
 // through the field's input specs, the last inverse pass (final) writes through its output specs.
 // Field f's arrays start at in + f * fstride, out + f * fstride.
-template <class R, int B, int CH, int NT, int REP>
+// NBT > 0 fixes nb = NBT at compile time for one-chunk passes (NBT - 1 <= CH forward, NBT <= CH inverse):
+// the loops unroll, every coefficient index j q mod P is a constant, and the coefficients are read
+// from the parameter table itself (no shared table, no barrier unless the gather/scatter tables need one).
+template <class R>
+LGF_D cx<R> box_coef(const BoxTw<R> &tw, int n) {  // (cos, sin)(2 pi n / P) from W_P^n
+  return cx<R>{tw.w[n].re, -tw.w[n].im};
+}
+
+template <class R, int B, int CH, int NT, int REP, int NBT = 0>
 __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
                                                  int gather, int nchunk, FwdSpecs sp) {
   constexpr int B3 = B * B * B;
-  __shared__ cx<R> TW[BOX_NB_MAX][CH];  // (cos, sin)(2 pi j q / P) of the chunk's general slots
-  const int nb = g.nb[ax], P = 2 * nb, half = nb;
+  constexpr bool FIX = NBT > 0;
+  __shared__ cx<R> TW[FIX ? 1 : BOX_NB_MAX][CH];  // (cos, sin)(2 pi j q / P) of the chunk's general slots
+  const int nb = FIX ? NBT : g.nb[ax], P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
-  const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
+  const int field = FIX ? (int)blockIdx.z : (int)blockIdx.z / nchunk, chunk = FIX ? 0 : (int)blockIdx.z % nchunk;
   const int pxf = box_pxu(g, field);
   if (ax != 0 && l1 >= pxf) return;  // a line beyond this field's K1x range (l1 is K1x for y and z)
   const bool realx = ax == 0 && pxf < P;
   // general slots q = 1 .. half - 1 in chunks of CH; chunk 0 also sums the slots q = 0 and q = half
   const int q0 = 1 + chunk * CH;
-  const int nq = max(0, min(CH, half - q0));
+  const int nq = FIX ? NBT - 1 : max(0, min(CH, half - q0));
   const bool ends = chunk == 0;
-  for (int i = threadIdx.x; i < nb * CH; i += NT) {
-    const int j = i / CH, c = i % CH;
-    const int n = (j * (q0 + c)) % P;  // < 32 * 32: 32-bit
-    TW[j][c] = cx<R>{tw.w[n].re, -tw.w[n].im};
-  }
+  if (!FIX)
+    for (int i = threadIdx.x; i < nb * CH; i += NT) {
+      const int j = i / CH, c = i % CH;
+      const int n = (j * (q0 + c)) % P;  // < 32 * 32: 32-bit
+      TW[j][c] = box_coef(tw, n);
+    }
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
@@ -165,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
     }
   const cx<R> *src = in + field * fstride + lbase;
   cx<R> *dst = out + field * fstride + lbase;
-  __syncthreads();
+  if (!FIX || gather) __syncthreads();
   // REP groups of NT consecutive cells per CTA, one after the other (the table serves them all)
 #pragma unroll 1
   for (int rep = 0; rep < REP; ++rep) {
@@ -189,7 +199,6 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   };
   // j = 0: every coefficient is 1
   cx<R> x = fetch(0);
-  cx<R> xn = nb > 1 ? fetch(1) : cx_zero<R>();
   cx<R> A[CH], Bv[CH];
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
@@ -198,20 +207,32 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   }
   // slots 0 and half (coefficients 1 and (-1)^j) from the sums over even and odd j
   cx<R> Se = x, So = cx_zero<R>();
-  for (int j = 1; j < nb; ++j) {
-    x = xn;
-    if (j + 1 < nb) xn = fetch(j + 1);
+  auto accumulate = [&](int j, const cx<R> &xj) {
     if (ends) {
-      if (j & 1) So = cadd(So, x);
-      else Se = cadd(Se, x);
+      if (j & 1) So = cadd(So, xj);
+      else Se = cadd(Se, xj);
     }
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
       if (k < nq) {
-        const cx<R> w = TW[j][k];
-        A[k] = cx<R>{rfma(A[k].re, w.re, x.re), rfma(A[k].im, w.re, x.im)};
-        Bv[k] = cx<R>{rfma(Bv[k].re, w.im, x.re), rfma(Bv[k].im, w.im, x.im)};
+        const cx<R> w = FIX ? box_coef(tw, (j * (q0 + k)) % P) : TW[FIX ? 0 : j][k];
+        A[k] = cx<R>{rfma(A[k].re, w.re, xj.re), rfma(A[k].im, w.re, xj.im)};
+        Bv[k] = cx<R>{rfma(Bv[k].re, w.im, xj.re), rfma(Bv[k].im, w.im, xj.im)};
       }
+    }
+  };
+  if constexpr (FIX) {
+    cx<R> xs[NBT];
+#pragma unroll
+    for (int j = 1; j < NBT; ++j) xs[j] = fetch(j);
+#pragma unroll
+    for (int j = 1; j < NBT; ++j) accumulate(j, xs[j]);
+  } else {
+    cx<R> xn = nb > 1 ? fetch(1) : cx_zero<R>();
+    for (int j = 1; j < nb; ++j) {
+      x = xn;
+      if (j + 1 < nb) xn = fetch(j + 1);
+      accumulate(j, x);
     }
   }
   if (ends) {
@@ -230,27 +251,29 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   }
 }
 
-template <class R, int B, int CH, int NT, int REP>
+template <class R, int B, int CH, int NT, int REP, int NBT = 0>
 __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
                                                  int final, int nchunk, InvOuts<R> outs, double scale) {
   constexpr int B3 = B * B * B;
-  __shared__ cx<R> TW[BOX_NB_MAX][CH];  // (cos, sin)(2 pi q o / P) for the general input slots
-  const int nb = g.nb[ax], P = 2 * nb, half = nb;
+  constexpr bool FIX = NBT > 0;
+  __shared__ cx<R> TW[FIX ? 1 : BOX_NB_MAX][CH];  // (cos, sin)(2 pi q o / P) for the general input slots
+  const int nb = FIX ? NBT : g.nb[ax], P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
-  const int field = blockIdx.z / nchunk, chunk = blockIdx.z % nchunk;
+  const int field = FIX ? (int)blockIdx.z : (int)blockIdx.z / nchunk, chunk = FIX ? 0 : (int)blockIdx.z % nchunk;
   const int pxf = box_pxu(g, field);
   if (ax != 0 && l1 >= pxf) return;  // a line beyond this field's K1x range (l1 is K1x for y and z)
   const bool realx = ax == 0 && pxf < P;
   const int o0 = chunk * CH;
-  const int no = min(CH, nb - o0);
-  for (int i = threadIdx.x; i < half * CH; i += NT) {
-    const int q = i / CH, c = i % CH;
-    const int n = (q * (o0 + c)) % P;  // < 32 * 32: 32-bit
-    TW[q][c] = cx<R>{tw.w[n].re, -tw.w[n].im};
-  }
+  const int no = FIX ? NBT : min(CH, nb - o0);
+  if (!FIX)
+    for (int i = threadIdx.x; i < half * CH; i += NT) {
+      const int q = i / CH, c = i % CH;
+      const int n = (q * (o0 + c)) % P;  // < 32 * 32: 32-bit
+      TW[q][c] = box_coef(tw, n);
+    }
   const int64_t bsa = g.bs[ax] * (int64_t)B3;
   const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
@@ -284,7 +307,7 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
     SO[1][k] = ob;
     SX[1][k] = ab;
   }
-  __syncthreads();
+  if (!FIX || final) __syncthreads();
   // REP groups of NT consecutive cells per CTA, one after the other (the table serves them all)
 #pragma unroll 1
   for (int rep = 0; rep < REP; ++rep) {
@@ -300,11 +323,7 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   cx<R> y[CH];
 #pragma unroll
   for (int k = 0; k < CH; ++k) y[k] = ((o0 + k) & 1) ? csub(X0, Xh) : cadd(X0, Xh);
-  cx<R> na = cx_zero<R>(), nbv = cx_zero<R>();
-  if (half > 1) fetch(1, na, nbv);
-  for (int q = 1; q < half; ++q) {
-    const cx<R> xa = na, xb = nbv;
-    if (q + 1 < half) fetch(q + 1, na, nbv);
+  auto accumulate = [&](int q, const cx<R> &xa, const cx<R> &xb) {
     const cx<R> U = cadd(xa, xb), V = csub(xa, xb);
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
@@ -312,11 +331,26 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
         if (o0 + k == 0) {
           y[k] = cadd(y[k], U);
         } else {
-          const cx<R> w = TW[q][k];
+          const cx<R> w = FIX ? box_coef(tw, (q * (o0 + k)) % P) : TW[FIX ? 0 : q][k];
           y[k].re = rdot2(y[k].re, w.re, U.re, w.im, V.im, -1.0f);
           if (!realx) y[k].im = rdot2(y[k].im, w.re, U.im, w.im, V.re, 1.0f);
         }
       }
+    }
+  };
+  if constexpr (FIX) {
+    cx<R> xa[NBT], xb[NBT];
+#pragma unroll
+    for (int q = 1; q < NBT; ++q) fetch(q, xa[q], xb[q]);
+#pragma unroll
+    for (int q = 1; q < NBT; ++q) accumulate(q, xa[q], xb[q]);
+  } else {
+    cx<R> na = cx_zero<R>(), nbv = cx_zero<R>();
+    if (half > 1) fetch(1, na, nbv);
+    for (int q = 1; q < half; ++q) {
+      const cx<R> xa = na, xb = nbv;
+      if (q + 1 < half) fetch(q + 1, na, nbv);
+      accumulate(q, xa, xb);
     }
   }
   if (!final) {
