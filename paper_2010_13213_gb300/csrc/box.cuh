@@ -35,6 +35,11 @@ struct BoxGeom {
   int nc;       // fields [0, nc) of a launch are complex (K1x < Px); the others are real fields kept on
                 // the Hermitian half K1x <= Px/2
 };
+// Per-axis members picked by selects: indexing a kernel parameter's array with a runtime axis would copy
+// the whole struct to local memory.
+LGF_HD int geo_nb(const BoxGeom &g, int a) { return a == 0 ? g.nb[0] : (a == 1 ? g.nb[1] : g.nb[2]); }
+LGF_HD int geo_P(const BoxGeom &g, int a) { return a == 0 ? g.P[0] : (a == 1 ? g.P[1] : g.P[2]); }
+LGF_HD int64_t geo_bs(const BoxGeom &g, int a) { return a == 0 ? g.bs[0] : (a == 1 ? g.bs[1] : g.bs[2]); }
 // Block frequencies K1x a field keeps, and the most any field of the launch keeps.
 LGF_HD int box_pxu(const BoxGeom &g, int field) { return field < g.nc ? g.P[0] : g.P[0] / 2 + 1; }
 LGF_HD int box_pxmax(const BoxGeom &g) { return g.nc > 0 ? g.P[0] : g.P[0] / 2 + 1; }
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   constexpr int B3 = B * B * B;
   constexpr bool FIX = NBT > 0;
   __shared__ cx<R> TW[FIX ? 1 : BOX_NB_MAX][CH];  // (cos, sin)(2 pi j q / P) of the chunk's general slots
-  const int nb = FIX ? NBT : g.nb[ax], P = 2 * nb, half = nb;
+  const int nb = FIX ? NBT : geo_nb(g, ax), P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
@@ -148,8 +153,8 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
       const int n = (j * (q0 + c)) % P;  // < 32 * 32: 32-bit
       TW[j][c] = box_coef(tw, n);
     }
-  const int64_t bsa = g.bs[ax] * (int64_t)B3;
-  const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
+  const int64_t bsa = geo_bs(g, ax) * (int64_t)B3;
+  const int64_t lbase = ((int64_t)l1 * geo_bs(g, a1) + (int64_t)l2 * geo_bs(g, a2)) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   const int gbase = l1 * (a1 == 0 ? 1 : g.nb[0]) + l2 * (a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   InSpec s0{}, s1{}, s2{};
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   constexpr int B3 = B * B * B;
   constexpr bool FIX = NBT > 0;
   __shared__ cx<R> TW[FIX ? 1 : BOX_NB_MAX][CH];  // (cos, sin)(2 pi q o / P) for the general input slots
-  const int nb = FIX ? NBT : g.nb[ax], P = 2 * nb, half = nb;
+  const int nb = FIX ? NBT : geo_nb(g, ax), P = 2 * nb, half = nb;
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
   const int l1 = (int)blockIdx.y % e1, l2 = (int)blockIdx.y / e1;
@@ -274,8 +279,8 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
       const int n = (q * (o0 + c)) % P;  // < 32 * 32: 32-bit
       TW[q][c] = box_coef(tw, n);
     }
-  const int64_t bsa = g.bs[ax] * (int64_t)B3;
-  const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
+  const int64_t bsa = geo_bs(g, ax) * (int64_t)B3;
+  const int64_t lbase = ((int64_t)l1 * geo_bs(g, a1) + (int64_t)l2 * geo_bs(g, a2)) * B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   const int gbase = l1 * (a1 == 0 ? 1 : g.nb[0]) + l2 * (a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   OutSpec<R> ore{}, oim{};
@@ -379,9 +384,9 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
                                                     BoxGeom g, int ax, const cx<double> *__restrict__ wP,
                                                     const double *__restrict__ Gd, int K) {
   constexpr int B3 = B * B * B;
-  const int P = g.P[ax];
+  const int P = geo_P(g, ax);
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
-  const int e1 = g.P[a1];
+  const int e1 = geo_P(g, a1);
   const int64_t line = blockIdx.y;
   const int l1 = (int)(line % e1), l2 = (int)(line / e1);
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
     if (Gd) {
       int d[3];
       for (int a = 0; a < 3; ++a) {
-        const int Pc = g.P[a] * B, n = coord[a] * B + mloc[a];
+        const int Pc = geo_P(g, a) * B, n = coord[a] * B + mloc[a];
         d[a] = n <= Pc / 2 ? n : Pc - n;
       }
       return cx<double>{Gd[((int64_t)d[2] * K + d[1]) * K + d[0]], 0.0};

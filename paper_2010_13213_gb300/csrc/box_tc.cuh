@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
 
   const int a1 = ax == 0 ? 1 : 0, a2 = ax == 2 ? 1 : 2;
   const int e1 = ax == 0 ? ext.y : ext.x;
-  const int64_t bsa = g.bs[ax] * (int64_t)B3;
+  const int64_t bsa = geo_bs(g, ax) * (int64_t)B3;
   const int gsa = ax == 0 ? 1 : (ax == 1 ? g.nb[0] : g.nb[0] * g.nb[1]);
   const int gs1 = a1 == 0 ? 1 : g.nb[0];
   const int gs2 = a2 == 1 ? g.nb[0] : g.nb[0] * g.nb[1];
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_bdft_tc(const cx<R> *__restrict__ i
     const int pxf = box_pxu(g, field);
     if (ax != 0 && l1 >= pxf) continue;  // beyond this field's K1x range (uniform over the CTA)
     const bool realx = ax == 0 && pxf < g.P[0];
-    const int64_t lbase = ((int64_t)l1 * g.bs[a1] + (int64_t)l2 * g.bs[a2]) * B3;
+    const int64_t lbase = ((int64_t)l1 * geo_bs(g, a1) + (int64_t)l2 * geo_bs(g, a2)) * B3;
     const int gbase = l1 * gs1 + l2 * gs2;
     const int m = chunk * TC_ROWS + row;
     InSpec s0{}, s1{}, s2{};
