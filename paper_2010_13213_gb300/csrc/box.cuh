@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_bdft_fwd(const cx<R> *__restrict__ in, c
   for (int rep = 0; rep < REP; ++rep) {
   const int m = (blockIdx.x * REP + rep) * NT + threadIdx.x;
   auto fetch = [&](int j) -> cx<R> {
-    if (!gather) return src[j * bsa + m];
+    if (!gather) return ld_stream(src + j * bsa + m);  // dead after this pass: keep L2 for its output
     R re = RT<R>::zero(), im = RT<R>::zero();
     auto add = [&](const InSpec &q, int si) {
       const int idx = GI[si][j];
@@ -319,12 +319,13 @@ __global__ void __launch_bounds__(NT) k_bdft_inv(const cx<R> *__restrict__ in, c
   const int m = (blockIdx.x * REP + rep) * NT + threadIdx.x;
   const cx<R> *src = in + field * fstride + lbase + m;
   // general input slot q (1 <= q < half): X_q and X_{P-q}, the latter conj(X_q) for a real field
+  // the input is dead after this pass: streaming loads keep L2 for its output
   auto fetch = [&](int q, cx<R> &xa, cx<R> &xb) {
-    xa = src[q * bsa];
-    xb = realx ? conj(xa) : src[(P - q) * bsa];
+    xa = ld_stream(src + q * bsa);
+    xb = realx ? conj(xa) : ld_stream(src + (P - q) * bsa);
   };
   // slots 0 and half: coefficients 1 and (-1)^o
-  const cx<R> X0 = src[0], Xh = src[half * bsa];
+  const cx<R> X0 = ld_stream(src), Xh = ld_stream(src + half * bsa);
   cx<R> y[CH];
 #pragma unroll
   for (int k = 0; k < CH; ++k) y[k] = ((o0 + k) & 1) ? csub(X0, Xh) : cadd(X0, Xh);
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(mid_threads<R, B>(), 512 / (B * B)) k_box_mid(
 #pragma unroll
       for (int r = 0; r < NV; ++r) {
         const int i = in_idx(r);
-        v[r] = cmul(Yb[(i * B + l1) * B + l0], twl[e]);
+        v[r] = cmul(ld_stream(Yb + (i * B + l1) * B + l0), twl[e]);
         e += dez;
         if (e >= L) e -= L;
       }

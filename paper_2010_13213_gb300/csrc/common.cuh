@@ -310,6 +310,19 @@ LGF_D df ld_stream(const df *p) {
   const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
   return df{v.x, v.y};
 }
+// complex values: one 8- or 16-byte access (cx is aligned to its size)
+LGF_D cx<double> ld_stream(const cx<double> *p) {
+  const double2 v = __ldcs(reinterpret_cast<const double2 *>(p));
+  return cx<double>{v.x, v.y};
+}
+LGF_D cx<float> ld_stream(const cx<float> *p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+  return cx<float>{v.x, v.y};
+}
+LGF_D cx<df> ld_stream(const cx<df> *p) {
+  const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+  return cx<df>{df{v.x, v.y}, df{v.z, v.w}};
+}
 
 // ------------------------------------------------------------------ loads/stores of fields
 // dtype 0: double storage, 1: float storage, 2: the kernel's own arithmetic type R (internal buffers).
