@@ -107,10 +107,11 @@ def _phases(ph):
     return {n: float(v) for n, v in zip(PHASE_NAMES, ph) if v}
 
 
-CADD, CNORM, CMUL, DFMUL, RFMA, DOT2, DFADD = 16, 6, 38, 7, 12, 24, 14  # FP32 instructions of the
+CADD, CNORM, CMUL, CMUL_W8, DFMUL, RFMA, DOT2, DFADD = 16, 6, 38, 24, 7, 12, 24, 14  # FP32 instructions of the
 # double-float operations (common.cuh): lazy complex add, renormalisation of a complex value, complex
-# product, product by a real power-of-two-free constant, real multiply-add, real two-term dot product
-# with accumulation, renormalised real add (+ renormalisation)
+# product, product by W_8 or W_8^3 (two lazy sums, two lazy real products), product by a real
+# power-of-two-free constant, real multiply-add, real two-term dot product with accumulation,
+# renormalised real add (+ renormalisation)
 
 
 def _fwd_pass_inst(nb, lines, B3, both):
@@ -140,10 +141,14 @@ def df_box_instructions(B, nb, ncomp):
     px, py, pz = 2 * nx, 2 * ny, 2 * nz
     B3 = B ** 3
     lg = int(math.log2(B))
-    # radix-2 FFT of B points: twiddled butterflies except W = 1 and W = -i (an exact swap)
-    twiddled = sum(sum(1 for j in range(1, ln // 2) if j * (64 // ln) != 16) * (B // ln)
+    # radix-2 FFT of B points: twiddled butterflies except W = 1 and W = -i (an exact swap); W = W_8 and
+    # W_8^3 take two sums and two real products (CMUL_W8), the others a complex product
+    def _tw(cls):
+        return sum(sum(1 for j in range(1, ln // 2) if cls(j * (64 // ln))) * (B // ln)
                    for ln in [2 ** s for s in range(1, lg + 1)])
-    fft1d = twiddled * CMUL + (B // 2) * lg * 2 * CADD  # lazily added; no renormalisation between steps
+    w8 = _tw(lambda k: k in (8, 24))
+    general = _tw(lambda k: k not in (8, 16, 24))
+    fft1d = general * CMUL + w8 * CMUL_W8 + (B // 2) * lg * 2 * CADD  # lazily added; no renormalisation
     mid_block = 6 * B * B * fft1d + 2 * B3 * CMUL + B3 * 2 * DFMUL  # one twiddle product per cell each way
     dft = mid = 0
     fields = [px] * (ncomp // 2) + [px // 2 + 1] * (ncomp % 2)

@@ -267,6 +267,28 @@ LGF_HD constexpr int bitrev(int i) {
   return r;
 }
 
+// Real product x c with the double-float error term kept unnormalised (the butterflies that follow add
+// lazily); a plain product for the other arithmetics.
+LGF_D double rmul_lazy(double x, double c) { return x * c; }
+LGF_D float rmul_lazy(float x, float c) { return x * c; }
+LGF_D df rmul_lazy(df x, df c) {
+  const float p = __fmul_rn(x.hi, c.hi);
+  float e = __fmaf_rn(x.hi, c.hi, -p);
+  e = __fmaf_rn(x.lo, c.hi, e);
+  return {p, __fmaf_rn(x.hi, c.lo, e)};
+}
+// v W_8^k for k = 1 or 3 (forward, W_8 = e^{-i pi/4}) or its conjugate (inverse): with s = a + b and
+// d = b - a for v = a + ib and c = cos(pi/4), v W_8 = c (s + i d) and v W_8^3 = c (d - i s); the
+// conjugates are c (-d + i s) and -c (s + i d).  Two sums and two real products instead of a complex
+// product.
+template <class R, bool INV>
+LGF_D cx<R> mul_w8(cx<R> v, bool k3, const R &c) {
+  const R sm = radd(v.re, v.im), d = radd(v.im, -v.re);
+  const R cs = rmul_lazy(sm, c), cd = rmul_lazy(d, c);
+  if (!INV) return k3 ? cx<R>{cd, -cs} : cx<R>{cs, cd};
+  return k3 ? cx<R>{-cs, -cd} : cx<R>{-cd, cs};
+}
+
 // In-register radix-2 decimation-in-time FFT of length N (power of two <= 64), unnormalised.  NORM = false
 // leaves double-float outputs unrenormalised (hi + lo still exact: for callers whose next operations are
 // lazy sums and error-compensated products, which renormalise themselves).
@@ -291,6 +313,8 @@ LGF_D void fft_reg(cx<R> (&x)[N], const Tw64<R> &tw) {
         cx<R> v = x[i + j + len / 2];
         if (j * (64 / len) == 16)  // W = -i (forward) or +i (inverse): an exact swap
           v = INV ? cx<R>{-v.im, v.re} : cx<R>{v.im, -v.re};
+        else if (j * (64 / len) == 8 || j * (64 / len) == 24)  // W = W_8 or W_8^3 (or conjugates)
+          v = mul_w8<R, INV>(v, j * (64 / len) == 24, tw.c[8]);
         else if (j != 0)
           v = cmul(v, twiddle<R, 64, INV>(tw, j * (64 / len)));
         x[i + j] = cadd(u, v);
