@@ -146,3 +146,20 @@ def test_df32_field_conversions_across_exponents(L, tables, mode):
         got = S.blocks_to_box(phi, case["blocks"], 16, case["shape"])
         for c in range(2):
             assert rel(got[c], ref[c] * s) <= TOL[2], (k, c, rel(got[c], ref[c] * s))
+
+
+@pytest.mark.parametrize("precision", [0, 2, 1])
+@pytest.mark.parametrize("shape", [(8, 32, 56), (64, 96, 8)])
+def test_box_block_counts_every_pass_kernel(L, tables, precision, shape):
+    """Boxes of 7 x 4 x 1 and 1 x 12 x 8 blocks (B = 8; shape is [nz][ny][nx] cells): the DFT passes
+    with compile-time block counts (nb <= 6) and the runtime-count passes with one to three chunks of
+    pair slots / outputs (nb = 7, 8, 12), and the trivial nb = 1 axis, against the oracle; three
+    components (a complex and a Hermitian-half real field)."""
+    B = 8
+    box = S.random_box(shape, 31 + shape[0], 3)
+    blocks = S.box_blocks(shape, B)
+    ref = oracle.solve_box_fft(box, 0.5)
+    phi = solve(L, tables[8], [blocks], B, 0.5, S.box_to_blocks(box, blocks, B), precision, L.LGF_MAC_BOX)
+    got = S.blocks_to_box(phi, blocks, B, shape)
+    for c in range(3):
+        assert rel(got[c], ref[c]) <= TOL[precision], (c, rel(got[c], ref[c]))
