@@ -15,8 +15,9 @@
 // complex: two real fields ride as real and imaginary part (G is real).
 //
 // The block-index DFTs have P = 2 nb points of which only nb inputs (forward) or outputs (inverse)
-// are used; they are evaluated directly (W_P^{(j k) mod P} from a table), the forward in two halves of
-// nb outputs (even and odd k) to bound the accumulators.
+// are used; they are evaluated directly by conjugate pairs (real coefficients cos, sin of 2 pi j k / P),
+// a CTA taking a chunk of pair slots (forward) or outputs (inverse); for nb <= 6 the block count is a
+// compile-time constant and one chunk covers the line.
 #pragma once
 #include "common.cuh"
 
@@ -417,8 +418,9 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
 }
 
 // ------------------------------------------------------------------ fused twiddle + local FFT + kernel
-// One CTA of B^2 threads per (K1 block, field): Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat;
-// back.  Six line-FFT steps, thread t owning line (l0, l1) = (t % B, t / B) of each axis:
+// One CTA per (K1 block, field): Y'[m] = Y[m] W_Pc^{m.K1}; X = FFT_B^3(Y'); X *= Ghat; back.  Six
+// line-FFT steps over the B^2 lines (l0, l1) of each axis, one thread per line (two for FP32, see
+// MidSplit):
 //   0  z lines (x, y): global Y, twiddle, FFT_z              -> shared
 //   1  y lines (x, z): FFT_y                                 -> shared
 //   2  x lines (y, z): FFT_x, X Ghat, conjugate              (registers)
