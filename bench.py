@@ -278,6 +278,94 @@ def batch_line(L, torch, dev, steps, warmup):
     return out
 
 
+def heat_line(L, torch, dev, steps, warmup):
+    """Heat-kernel (integrating-factor) apply on the composite mesh (FIF-AMR, Sec. 3.5) in DF32: the
+    three-level ring (h = R/16, R/32, R/64; 3 components), alpha_finest = 0.1 and the per-level scaling
+    alpha_k = alpha_finest 4^-(K-1-k).  value = target cells of all levels / call time, L2 flushed
+    between calls.  Roofline of the separable passes + store (k_heat_line x 3 per level, k_heat_store):
+    in double-float the passes are bound by the FP32 pipe (about 20 r + 10 instructions against 16 bytes
+    per cell-component and pass), so the algorithmic count is per target cell-component and pass one
+    product, r lazy pair sums and r multiply-adds and a renormalisation, with r per level the radius the
+    library takes (the last n with e^{-2 alpha} I_n(2 alpha) >= 1e-18); the store counts nothing."""
+    import lgf_synth as S
+    mesh, f = S.three_level_ring()
+    m = L.Mesh(mesh["levels"], mesh["B"], mesh["h0"], n_ext=mesh["n_ext"])
+    ncomp = f[0].shape[0]
+    ft = torch.from_numpy(np.concatenate(f, axis=1)).to(dev)
+    g = torch.zeros_like(ft)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hs = torch.cuda.Stream(dev)
+    st = hs.cuda_stream
+
+    def apply(rep=None, timing=0):
+        L.lgf_heat_apply(None, m, ncomp, ft.data_ptr(), g.data_ptr(), L.LGF_F64, 0.1,
+                         L.make_opts(precision=L.LGF_PREC_DF32, timing=timing), rep, st)
+
+    ref = L.lgf_report()
+    apply(ref)
+    for _ in range(warmup):
+        apply()
+    torch.cuda.synchronize()
+    evs = []
+    with torch.cuda.stream(hs):
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(hs)
+            apply()
+            e1.record(hs)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    ph = []
+    rep = L.lgf_report()
+    for _ in range(steps):
+        with torch.cuda.stream(hs):
+            flush.fill_(1.0)
+        apply(rep, timing=1)
+        ph.append([rep.ms_phase[i] for i in range(8)])
+    torch.cuda.synchronize()
+    ph = np.mean(np.array(ph), axis=0)
+    # end to end through the C ABI: pinned host source in, result out, inside the timed region
+    h_in = torch.from_numpy(np.concatenate(f, axis=1)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(hs):
+        e0.record(hs)
+        for _ in range(steps):
+            ft.copy_(h_in, non_blocking=True)
+            apply()
+            h_out.copy_(g, non_blocking=True)
+        e1.record(hs)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / steps
+    cells = int(ref.target_cells)
+    from scipy.special import ive
+    K = len(mesh["levels"])
+    n_blk = [len(b) for b in mesh["levels"]] + [0]
+    inst = 0
+    for k in range(K):
+        a2 = 2 * 0.1 * 4.0 ** (-(K - 1 - k))
+        r = max([n for n in range(80) if ive(n, a2) >= 1e-18] or [0])
+        omega = (n_blk[k] - n_blk[k + 1] // 8) * mesh["B"] ** 3
+        inst += 3 * ncomp * omega * (DFMUL + r * (CADD // 2 + RFMA) + CNORM // 2)
+    ach = inst / (ph[7] * 1e-3)
+    return {"workload": "three-level ring (config 3 mesh: h = R/16, R/32, R/64, 16^3 blocks), 3 components, "
+                        "alpha_finest = 0.1, DF32", "blocks": int(m.total_blocks), "target_cells": cells,
+            "ms_per_step": ms, "value": cells / (ms * 1e-3) / 1e6, "unit": "Mcells/s", "dtype": "df32",
+            "phases_ms": {"restrict": float(ph[0]), "build": float(ph[5]), "passes_and_store": float(ph[7])},
+            "gpu_launches": int(ref.kernel_launches),
+            "roofline": {"kernel": "k_heat_line x 3 + k_heat_store (per level)", "bound": "alu",
+                         "achieved": ach / 1e12, "peak": FP32_INST_PEAK / 1e12, "unit": "T FP32-inst/s",
+                         "frac": ach / FP32_INST_PEAK, "traffic": None,
+                         "note": "algorithmic FP32 instructions of the double-float passes on the target cells "
+                                 "(halo cells not counted) over the library's phase time of the passes and the "
+                                 "store; peak = 152 SMs x 128 FP32 lanes x 2070 MHz (derived, not measured)"},
+            "e2e": {"value": cells / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s",
+                    "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)},
+            "l2": "flushed by a 256 MiB write between timed calls (outside the events)"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -418,6 +506,7 @@ def run_gpu(args):
     ms_df, ms_64, e2e_ms, e2e_serial_ms = vals.tolist()
     L.lgf_table_destroy(table)
     batch = batch_line(L, torch, dev, 5, 2) if args.batch else None
+    heat = heat_line(L, torch, dev, 10, 3) if args.batch else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -460,6 +549,7 @@ def run_gpu(args):
         "e2e_serial": {"value": cells * world / (e2e_serial_ms * 1e-3) / 1e6, "unit": "Mcells/s",
                        "note": "one stream: copy in, solve, copy out, step after step"},
         "batch_rk3_stage": batch,
+        "heat_apply": heat,
         "gpu_launches": int(rep_df.kernel_launches) * args.steps,
         "clocks": clocks,
         "wall_s_timed": {"df32": wall_df, "fp64": wall_64, "fp32": wall_32},
@@ -476,15 +566,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "pair", "box"])
-    ap.add_argument("--batch", default=1, type=int, help="also time the 64-instance batched RK3 stage (0: skip)")
-    ap.add_argument("--workload", default="ring", choices=["ring", "batch"],
-                    help="batch: only the 64-instance batched RK3 stage (its own JSON line)")
+    ap.add_argument("--batch", default=1, type=int,
+                    help="also time the 64-instance batched RK3 stage and the composite-mesh heat apply (0: skip)")
+    ap.add_argument("--workload", default="ring", choices=["ring", "batch", "heat"],
+                    help="batch: only the 64-instance batched RK3 stage; heat: only the composite-mesh "
+                         "heat apply (each its own JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch_only(args)
+    elif args.workload == "heat":
+        run_heat_only(args)
     else:
         run_gpu(args)
 
@@ -501,6 +595,22 @@ def run_batch_only(args):
                 "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": out["ms_per_stage"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "df32", "data": "synthetic", "config": out}
+        print(json.dumps(line), flush=True)
+
+
+def run_heat_only(args):
+    """The composite-mesh heat apply alone (one replica per rank), printed by rank 0."""
+    import torch
+    import paper_2010_13213_gb300.lgf as L
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    out = heat_line(L, torch, torch.device("cuda", local), args.steps, args.warmup)
+    if rank == 0:
+        line = {"metric": "heat-kernel apply (FIF-AMR), target Mcells/s", "value": out["value"] * world,
+                "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": out["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "df32", "data": "synthetic", "config": out,
+                "roofline": out["roofline"], "e2e": out["e2e"], "gpu_launches": out["gpu_launches"] * args.steps}
         print(json.dumps(line), flush=True)
 
 

@@ -262,10 +262,84 @@ __global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *bloc
   }
 }
 
-// One separable pass of E_alpha along `axis` over the heat block set; absent neighbours read 0.
-// When the kernel radius fits in a block (r <= B) every tap reads this block or one of its two
-// neighbours along the axis, looked up once per CTA; wider kernels look each cell up in the block map.
-// Sums run unnormalised in double-float (renormalised once per cell).
+// One separable pass of E_alpha along `axis` over the heat block set, for kernel radii r <= B (every
+// tap reads this block or one of its two neighbours along the axis).  The CTA stages the block and the
+// r cells of each neighbour block next to it (zeros where a neighbour is absent) in shared memory as
+// S[t][q]: t = la + r in [0, B + 2r) the position along the axis, q in [0, B^2) the line (the other two
+// coordinates); rows padded to B^2 + 1.  Thread q then sums its line's B outputs from shared memory,
+// symmetric taps paired, in double-float left unnormalised until the end, and the outputs go back to
+// global memory through shared memory in the block's element order (coalesced).
+// grid (|HB|, ncomp), B^2 threads, (B + 2r)(B^2 + 1) values of dynamic shared memory.
+template <class R, int B>
+__global__ void __launch_bounds__(B * B) k_heat_line(LevelDev L, const int4 *blocks, const int32_t *HB, int axis,
+                                                     const R *in, R *out, int64_t cs, HeatW w) {
+  constexpr int B2 = B * B, B3 = B * B2, SH = B == 8 ? 3 : 4, QS = B2 + 1;
+  static_assert(B == 8 || B == 16, "block size");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *S = reinterpret_cast<R *>(smem_raw);
+  __shared__ R wt[B + 1];
+  const int r = w.r, T = B + 2 * r;
+  const int b = HB[blockIdx.x], comp = blockIdx.y;
+  const int4 bc = blocks[b];
+  for (int d = threadIdx.x; d <= r; d += B2) wt[d] = RT<R>::from(w.w[d]);
+  const int ex = axis == 0, ey = axis == 1, ez = axis == 2;
+  const int nbm = level_block(L, bc.x - ex, bc.y - ey, bc.z - ez);
+  const int nbp = level_block(L, bc.x + ex, bc.y + ey, bc.z + ez);
+  const R *src = in + comp * cs;
+  // e / T for e < T B^2 <= 48 * 256 by a multiply and shift (exact: the rounding of the reciprocal adds
+  // less than e / 2^20 < 1 / T)
+  const unsigned invT = ((1u << 20) + (unsigned)T - 1) / (unsigned)T;
+  // staging order: consecutive e are consecutive in memory (x fastest; along x the axis runs fastest)
+  for (int e = threadIdx.x; e < T * B2; e += B2) {
+    int t, q, x, y, z;
+    if (axis == 0) {
+      q = (int)(((unsigned)e * invT) >> 20);
+      t = e - q * T;
+      y = q & (B - 1), z = q >> SH, x = t - r;
+    } else if (axis == 1) {
+      const int u = e >> SH, zz = (int)(((unsigned)u * invT) >> 20);
+      x = e & (B - 1), t = u - zz * T, z = zz, y = t - r;
+      q = x + B * z;
+    } else {
+      x = e & (B - 1), y = (e >> SH) & (B - 1), t = e >> (2 * SH), z = t - r;
+      q = x + B * y;
+    }
+    const int la = t - r;  // in [-r, B + r)
+    const int blk = la < 0 ? nbm : (la >= B ? nbp : b);
+    const int sh = la < 0 ? B : (la >= B ? -B : 0);  // into the neighbour's local coordinates
+    if (axis == 0) x += sh;
+    else if (axis == 1) y += sh;
+    else z += sh;
+    S[t * QS + q] = blk >= 0 ? src[(int64_t)blk * B3 + ((z * B + y) * B + x)] : RT<R>::zero();
+  }
+  __syncthreads();
+  const int q = threadIdx.x;
+  R acc[B];
+  const R w0 = wt[0];
+#pragma unroll
+  for (int la = 0; la < B; ++la) acc[la] = w0 * S[(la + r) * QS + q];
+  for (int d = 1; d <= r; ++d) {
+    const R wd = wt[d];
+    const R *Sp = S + (r + d) * QS + q, *Sm = S + (r - d) * QS + q;
+#pragma unroll
+    for (int la = 0; la < B; ++la) acc[la] = rfma(acc[la], wd, radd(Sp[la * QS], Sm[la * QS]));
+  }
+  __syncthreads();  // every read of the tile is done before it is overwritten
+#pragma unroll
+  for (int la = 0; la < B; ++la) S[la * QS + q] = rnorm(acc[la]);
+  __syncthreads();
+  R *dst = out + comp * cs + (int64_t)b * B3;
+  for (int off = threadIdx.x; off < B3; off += B2) {
+    const int x = off & (B - 1), y = (off >> SH) & (B - 1), z = off >> (2 * SH);
+    const int la = axis == 0 ? x : (axis == 1 ? y : z);
+    const int ql = axis == 0 ? y + B * z : (axis == 1 ? x + B * z : x + B * y);
+    dst[off] = S[la * QS + ql];
+  }
+}
+template <class R, int B>
+size_t heat_line_smem(int r) { return sizeof(R) * (size_t)(B + 2 * r) * (B * B + 1); }
+
+// The same pass for radii r > B: every tap looks its cell up in the block map; absent cells read 0.
 template <class R>
 __global__ void __launch_bounds__(256) k_heat_pass(LevelDev L, const int4 *blocks, const int32_t *HB, int axis,
                                                    const R *in, R *out, int64_t cs, HeatW w) {
@@ -276,33 +350,6 @@ __global__ void __launch_bounds__(256) k_heat_pass(LevelDev L, const int4 *block
   for (int d = threadIdx.x; d <= w.r; d += blockDim.x) wt[d] = RT<R>::from(w.w[d]);
   __syncthreads();
   const R *src = in + comp * cs;
-  if (w.r <= B) {
-    const int ex = axis == 0, ey = axis == 1, ez = axis == 2;
-    const int nbm = level_block(L, bc.x - ex, bc.y - ey, bc.z - ez);
-    const int nbp = level_block(L, bc.x + ex, bc.y + ey, bc.z + ez);
-    const int st = 1 << (axis * sh);  // element stride along the axis inside a block
-    // tap d reads element la + d (la - d) of this line: this block, or the neighbour at local la + d - B
-    // (la - d + B); a missing neighbour contributes 0.  Addresses are selected, not branched, and four
-    // taps are unrolled so their loads are in flight together.
-    const int64_t bp = nbp >= 0 ? (int64_t)(nbp - b) * B3 - (int64_t)B * st : 0;  // + own + d st
-    const int64_t bm = nbm >= 0 ? (int64_t)(nbm - b) * B3 + (int64_t)B * st : 0;  // + own - d st
-    for (int off = threadIdx.x; off < B3; off += blockDim.x) {
-      const int la = (off >> (axis * sh)) & (B - 1);
-      const int64_t own = (int64_t)b * B3 + off;
-      R acc = wt[0] * src[own];
-#pragma unroll 4
-      for (int d = 1; d <= w.r; ++d) {
-        const bool inp = la + d < B, inm = la - d >= 0;
-        const bool okp = inp || nbp >= 0, okm = inm || nbm >= 0;
-        const int64_t ip = own + d * st + (inp ? 0 : bp), im = own - d * st + (inm ? 0 : bm);
-        const R vp = okp ? src[ip] : RT<R>::zero();
-        const R vm = okm ? src[im] : RT<R>::zero();
-        acc = rfma(acc, wt[d], radd(vp, vm));
-      }
-      out[comp * cs + own] = rnorm(acc);
-    }
-    return;
-  }
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
               z = (bc.z << sh) + (off >> (2 * sh));

@@ -443,6 +443,31 @@ static int heat_weights(double alpha, HeatW *w) {
   return LGF_OK;
 }
 
+// One separable heat pass over a level's heat block set: the shared-memory line kernel for radii up to
+// B, the block-map lookup kernel beyond.
+template <class R, int BB>
+static int heat_line_launch(const LevelDev &Ld, const int4 *BL, const int32_t *HB, int nHB, int ncomp, int ax,
+                            const R *in, R *out, int64_t cs, const HeatW &w, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_heat_line<R, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)heat_line_smem<R, BB>(BB));
+    attr = true;
+  }
+  k_heat_line<R, BB><<<dim3(nHB, ncomp), BB * BB, heat_line_smem<R, BB>(w.r), st>>>(Ld, BL, HB, ax, in, out, cs, w);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "heat pass launch: %s", cudaGetErrorString(e));
+}
+template <class R>
+static int heat_pass_launch(int B, const LevelDev &Ld, const int4 *BL, const int32_t *HB, int nHB, int ncomp, int ax,
+                            const R *in, R *out, int64_t cs, const HeatW &w, cudaStream_t st) {
+  if (w.r <= B && B == 16) return heat_line_launch<R, 16>(Ld, BL, HB, nHB, ncomp, ax, in, out, cs, w, st);
+  if (w.r <= B && B == 8) return heat_line_launch<R, 8>(Ld, BL, HB, nHB, ncomp, ax, in, out, cs, w, st);
+  k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, BL, HB, ax, in, out, cs, w);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "heat pass launch: %s", cudaGetErrorString(e));
+}
+
 template <class R>
 static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype, double alpha,
                   const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
@@ -509,12 +534,12 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
                                                       cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
     LGF_LAUNCH_CHECK("heat source");
     tm.mark(PH_INTERP);
-    k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 0, T0, T1, cs[k], W[k]);
-    LGF_LAUNCH_CHECK("heat x");
-    k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 1, T1, T0, cs[k], W[k]);
-    LGF_LAUNCH_CHECK("heat y");
-    k_heat_pass<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 2, T0, T1, cs[k], W[k]);
-    LGF_LAUNCH_CHECK("heat z");
+    for (int ax = 0; ax < 3; ++ax) {  // x: T0 -> T1, y: T1 -> T0, z: T0 -> T1
+      const R *hin = ax == 1 ? T1 : T0;
+      R *hout = ax == 1 ? T0 : T1;
+      if ((rc = heat_pass_launch<R>(B, Ld, L.d_BL, HB, nHB, ncomp, ax, hin, hout, cs[k], W[k], st))) return rc;
+      ++launches;
+    }
     k_heat_store<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, T1, cs[k], g, dtype, ucs, L.user_off);
     LGF_LAUNCH_CHECK("heat store");
     tm.mark(PH_HEAT);

@@ -120,17 +120,17 @@ def test_three_level_ring(L, table8, ring3, precision):
     assert rep.residual_rel < (5e-9 if precision == 0 else 5e-7)
 
 
-def gpu_heat(L, mesh, f_levels, alpha, precision, table=None):
+def gpu_heat(L, mesh, f_levels, alpha, precision, table=None, rep=None):
     m = L.Mesh(mesh["levels"], mesh["B"], mesh["h0"], n_ext=mesh["n_ext"])
     f = torch.from_numpy(flat(f_levels)).cuda()
     g = torch.full_like(f, float("nan"))
     L.lgf_heat_apply(table, m, f.shape[0], f.data_ptr(), g.data_ptr(), L.LGF_F64, alpha,
-                     L.make_opts(precision=precision))
+                     L.make_opts(precision=precision), rep)
     torch.cuda.synchronize()
     return split(g.cpu().numpy(), mesh)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (2, 1e-12), (1, 1e-6)])
 def test_heat_two_level(L, precision, tol):
     mesh = two_level()
     rng = np.random.default_rng(31)
@@ -139,8 +139,12 @@ def test_heat_two_level(L, precision, tol):
     lv = amr.build_levels(mesh)
     masks = [amr._to_blocks(lv[k], mesh["levels"][k], lv[k].omega[None].astype(float), 8)[0] > 0.5
              for k in range(2)]
-    got = gpu_heat(L, mesh, f, 0.1, precision)
+    rep = L.lgf_report()
+    got = gpu_heat(L, mesh, f, 0.1, precision, rep=rep)
     assert rel_err_levels(got, ref, masks) <= tol
+    # restriction (2) + coarsening (1) + level 0 (coarse-part build, source build, 3 passes, store) +
+    # level 1 (source build, 3 passes, store)
+    assert rep.kernel_launches == 14
 
 
 def test_heat_single_level_with_table_workspace(L, table8):
