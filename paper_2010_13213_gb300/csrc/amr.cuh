@@ -61,22 +61,24 @@ LGF_D R lap7(const LevelDev &L, const R *buf, int64_t cs, int comp, int x, int y
   return (s - RT<R>::from(6.0) * c) * inv_h2;
 }
 
-// P_{k-1->k}: fine cell (fx, fy, fz) -> sum over the 8 coarse corners of prod (3/4 | 1/4) * value
+// P_{k-1->k}: fine cell (fx, fy, fz) -> sum over the 8 coarse corners of prod (3/4 | 1/4) * value.  The
+// weights are 27, 9, 3 or 1 / 64 (exact floats); products and sums run lazily in double-float, with one
+// renormalisation at the end.
 template <class R, class F>
 LGF_D R interp_at(int fx, int fy, int fz, F coarse_value) {
   const int px = fx >> 1, py = fy >> 1, pz = fz >> 1;
   const int qx = (fx & 1) ? px + 1 : px - 1;
   const int qy = (fy & 1) ? py + 1 : py - 1;
   const int qz = (fz & 1) ? pz + 1 : pz - 1;
-  const R w3 = RT<R>::from(0.75), w1 = RT<R>::from(0.25);
   R acc = RT<R>::zero();
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int cx = (c & 1) ? qx : px, cy = (c & 2) ? qy : py, cz = (c & 4) ? qz : pz;
-    const R w = ((c & 1) ? w1 : w3) * ((c & 2) ? w1 : w3) * ((c & 4) ? w1 : w3);
-    acc = acc + w * coarse_value(cx, cy, cz);
+    const int quarters = ((c & 1) != 0) + ((c & 2) != 0) + ((c & 4) != 0);  // factors 1/4 (the others 3/4)
+    const float w = quarters == 0 ? 27.0f / 64 : (quarters == 1 ? 9.0f / 64 : (quarters == 2 ? 3.0f / 64 : 1.0f / 64));
+    acc = radd(acc, rscale(coarse_value(cx, cy, cz), w));
   }
-  return acc;
+  return rnorm(acc);
 }
 
 // ------------------------------------------------------------------ restriction (step 1)

@@ -234,6 +234,14 @@ LGF_D double rdot2(double acc, double a, double b, double c, double d, float sgn
 }
 LGF_D float rdot2(float acc, float a, float b, float c, float d, float sgn) { return fmaf(a, b, fmaf(sgn * c, d, acc)); }
 LGF_D df rdot2(df acc, df a, df b, df c, df d, float sgn) { return df_dot2_acc_lazy(acc, a, b, c, d, sgn); }
+// x w for a float w of few significant bits (an interpolation weight): the product error is kept
+// (TwoProd on the high part), the result left unnormalised
+LGF_D double rscale(double x, float w) { return x * (double)w; }
+LGF_D float rscale(float x, float w) { return x * w; }
+LGF_D df rscale(df x, float w) {
+  const float p = __fmul_rn(x.hi, w);
+  return {p, __fmaf_rn(x.lo, w, __fmaf_rn(x.hi, w, -p))};
+}
 LGF_D double radd(double a, double b) { return a + b; }
 LGF_D float radd(float a, float b) { return a + b; }
 LGF_D df radd(df a, df b) { return df_add_lazy(a, b); }
