@@ -40,6 +40,39 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(vals, world, device=None):
+    """Element-wise maximum of per-rank values (step times) over the replicas of the job, on whatever
+    process group is initialised (NCCL on the GPU machine, gloo in the CPU tests); unchanged on one rank."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_rate(units_per_rank, ms, world):
+    """Whole-job throughput in M units/s of `world` replicas that each process `units_per_rank` units per
+    step, a step taking `ms` milliseconds (the maximum over ranks)."""
+    return units_per_rank * world / (ms * 1e-3) / 1e6
+
+
+def _replicas_init(world, local):
+    """Process group of the replicas (torchrun, one rank per GPU) for the barrier and the max over ranks."""
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        dist.barrier()
+
+
+def _replicas_done(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -499,11 +532,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
-    # max over ranks
-    vals = torch.tensor([ms_df, ms_64, e2e_ms, e2e_serial_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_df, ms_64, e2e_ms, e2e_serial_ms = vals.tolist()
+    # every reported time is the maximum over the replicas
+    tc_names = sorted(tc)
+    mx = max_over_ranks([ms_df, ms_64, ms_32, ms_dfp, e2e_ms, e2e_serial_ms] + [tc[n][0] for n in tc_names], world, dev)
+    ms_df, ms_64, ms_32, ms_dfp, e2e_ms, e2e_serial_ms = mx[:6]
+    tc = {n: (mx[6 + i],) + tuple(tc[n][1:]) for i, n in enumerate(tc_names)}
     L.lgf_table_destroy(table)
     batch = batch_line(L, torch, dev, 5, 2) if args.batch else None
     heat = heat_line(L, torch, dev, 10, 3) if args.batch else None
@@ -518,7 +551,7 @@ def run_gpu(args):
     cpu_dt = time.perf_counter() - t0
     import oracle
     line = {
-        "metric": METRIC, "value": cells * world / (ms_df * 1e-3) / 1e6, "unit": "Mcells/s",
+        "metric": METRIC, "value": replica_rate(cells, ms_df, world), "unit": "Mcells/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_df,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32",
         "data": "synthetic",
@@ -526,13 +559,13 @@ def run_gpu(args):
                    "mac_mode": args.mode, "parallelism": f"replicas{world}",
                    "l2": "flushed by a 256 MiB write between timed steps (outside the step events)"},
         "rel_err": errs,
-        "fp64": {"value": cells * world / (ms_64 * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": ms_64,
+        "fp64": {"value": replica_rate(cells, ms_64, world), "unit": "Mcells/s", "ms_per_step": ms_64,
                  "mode": MODE_NAMES[rep_64.mac_mode_used], "phases_ms": _phases(ph_64)},
-        "fp32": {"value": cells * world / (ms_32 * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": ms_32,
+        "fp32": {"value": replica_rate(cells, ms_32, world), "unit": "Mcells/s", "ms_per_step": ms_32,
                  "rel_err": errs["fp32"], "note": "plain FP32: error above the 1e-10 target, reported only"},
-        "df32_pair_mode": {"value": cells * world / (ms_dfp * 1e-3) / 1e6, "unit": "Mcells/s",
+        "df32_pair_mode": {"value": replica_rate(cells, ms_dfp, world), "unit": "Mcells/s",
                            "ms_per_step": ms_dfp, "phases_ms": _phases(ph_dfp)},
-        "dft_gemm": {name: {"value": cells * world / (v[0] * 1e-3) / 1e6, "unit": "Mcells/s", "ms_per_step": v[0],
+        "dft_gemm": {name: {"value": replica_rate(cells, v[0], world), "unit": "Mcells/s", "ms_per_step": v[0],
                             "rel_err": errs[name], "phases_ms": _phases(v[1])} for name, v in tc.items()},
         "mode": MODE_NAMES[rep_df.mac_mode_used],
         "phases_ms_df32": _phases(ph_df),
@@ -542,11 +575,11 @@ def run_gpu(args):
         "cpu_baseline": {"value": cells / cpu_dt / 1e6, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
                          "sample": "full workload once: zero-padded FP64 FFT convolution (pocketfft)",
                          "threads_used": oracle.num_threads()},
-        "e2e": {"value": cells * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s",
+        "e2e": {"value": replica_rate(cells, e2e_ms, world), "unit": "Mcells/s",
                 "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8),
                 "note": "pinned host source copied in and the result copied out every step; consecutive steps"
                         " on two streams, so a step's copies overlap the neighbouring step's solve"},
-        "e2e_serial": {"value": cells * world / (e2e_serial_ms * 1e-3) / 1e6, "unit": "Mcells/s",
+        "e2e_serial": {"value": replica_rate(cells, e2e_serial_ms, world), "unit": "Mcells/s",
                        "note": "one stream: copy in, solve, copy out, step after step"},
         "batch_rk3_stage": batch,
         "heat_apply": heat,
@@ -589,13 +622,18 @@ def run_batch_only(args):
     import paper_2010_13213_gb300.lgf as L
     rank, world, local = _env_rank()
     torch.cuda.set_device(local)
-    out = batch_line(L, torch, torch.device("cuda", local), args.steps, args.warmup)
+    dev = torch.device("cuda", local)
+    _replicas_init(world, local)
+    out = batch_line(L, torch, dev, args.steps, args.warmup)
+    ms = max_over_ranks([out["ms_per_stage"]], world, dev)[0]
     if rank == 0:
-        line = {"metric": "batched RK3 stage, Poisson target Mcells/s", "value": out["value"] * world,
+        line = {"metric": "batched RK3 stage, Poisson target Mcells/s",
+                "value": replica_rate(out["target_cells_per_stage"], ms, world),
                 "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": out["ms_per_stage"], "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "df32", "data": "synthetic", "config": out}
         print(json.dumps(line), flush=True)
+    _replicas_done(world)
 
 
 def run_heat_only(args):
@@ -604,14 +642,19 @@ def run_heat_only(args):
     import paper_2010_13213_gb300.lgf as L
     rank, world, local = _env_rank()
     torch.cuda.set_device(local)
-    out = heat_line(L, torch, torch.device("cuda", local), args.steps, args.warmup)
+    dev = torch.device("cuda", local)
+    _replicas_init(world, local)
+    out = heat_line(L, torch, dev, args.steps, args.warmup)
+    ms = max_over_ranks([out["ms_per_step"]], world, dev)[0]
     if rank == 0:
-        line = {"metric": "heat-kernel apply (FIF-AMR), target Mcells/s", "value": out["value"] * world,
+        line = {"metric": "heat-kernel apply (FIF-AMR), target Mcells/s",
+                "value": replica_rate(out["target_cells"], ms, world),
                 "unit": "Mcells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": out["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "df32", "data": "synthetic", "config": out,
                 "roofline": out["roofline"], "e2e": out["e2e"], "gpu_launches": out["gpu_launches"] * args.steps}
         print(json.dumps(line), flush=True)
+    _replicas_done(world)
 
 
 if __name__ == "__main__":
