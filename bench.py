@@ -399,6 +399,54 @@ def heat_line(L, torch, dev, steps, warmup):
             "l2": "flushed by a 256 MiB write between timed calls (outside the events)"}
 
 
+def refresh_line(L, torch, dev, case, steps, warmup):
+    """Velocity refresh u = -C^T L_E^{-1} omega (Sec. 4.1, Eq. (eq:vel_update)) of the ring vorticity of the
+    solve workload (96 x 96 x 48 cells, 16^3 blocks, the three components as edge vorticity): the DF32
+    streamfunction solve on the blocks and their -x, -y, -z neighbours (7 x 7 x 4 blocks of box) plus the
+    curl kernel.  Error against the oracle's refresh (outside the timed region); value = cells / call
+    time, L2 flushed between calls."""
+    import oracle.refresh as OR
+    B, h = case["B"], case["h"]
+    cells = int(np.prod(case["shape"]))
+    table = L.lgf_table_create(B, (6, 6, 3), L.LGF_TBL_BOX_ONLY)
+    m = L.Mesh([case["blocks"]], B, h)
+    om = torch.from_numpy(case["f"]).to(dev)
+    u = torch.zeros_like(om)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    rs = torch.cuda.Stream(dev)
+    opts = L.make_opts(precision=L.LGF_PREC_DF32)
+    rep = L.lgf_report()
+
+    def call(r=None):
+        L.lgf_velocity_refresh(table, m, om.data_ptr(), u.data_ptr(), L.LGF_F64, opts, r, rs.cuda_stream)
+
+    call(rep)
+    torch.cuda.synchronize()
+    import lgf_synth as S
+    got = S.blocks_to_box(u.cpu().numpy(), case["blocks"], B, case["shape"])
+    ref = OR.velocity_refresh(case["box"], h)
+    err = float(max(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max() for c in range(3)))
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    evs = []
+    with torch.cuda.stream(rs):
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(rs)
+            call()
+            e1.record(rs)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    L.lgf_table_destroy(table)
+    return {"workload": "ring vorticity 96x96x48 cells (edge components), 16^3 blocks, DF32, box mode",
+            "ms_per_step": ms, "value": cells / (ms * 1e-3) / 1e6, "unit": "Mcells/s", "rel_err": err,
+            "gpu_launches": int(rep.kernel_launches), "dtype": "df32",
+            "l2": "flushed by a 256 MiB write between timed calls (outside the events)"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -540,6 +588,7 @@ def run_gpu(args):
     L.lgf_table_destroy(table)
     batch = batch_line(L, torch, dev, 5, 2) if args.batch else None
     heat = heat_line(L, torch, dev, 10, 3) if args.batch else None
+    vref = refresh_line(L, torch, dev, case, 10, 3) if args.batch else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -583,6 +632,7 @@ def run_gpu(args):
                        "note": "one stream: copy in, solve, copy out, step after step"},
         "batch_rk3_stage": batch,
         "heat_apply": heat,
+        "velocity_refresh": vref,
         "gpu_launches": int(rep_df.kernel_launches) * args.steps,
         "clocks": clocks,
         "wall_s_timed": {"df32": wall_df, "fp64": wall_64, "fp32": wall_32},

@@ -184,6 +184,27 @@ int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f
                    lgf_report *rep, void *cuda_stream);
 
 /*
+ * lgf_velocity_refresh -- velocity from vorticity on one level (Sec. 4.1, Eq. (eq:vel_update)):
+ * u = -C^T L_E^{-1} omega.  Staggered lattice (Sec. 2.1): component a of cell n is stored at index n,
+ * the velocity at the face centre n + (1,1,1)/2 + e_a/2, the vorticity (and the streamfunction) at the
+ * edge centre n + (1,1,1) - e_a/2 (in cells).  L_E^{-1} is the free-space LGF solve of each edge
+ * component; C^T (= the edge-to-face curl, the transpose of the face-to-edge curl C, Eq. (eq:mimetic)) is
+ *   (C^T psi)_x[n] = (psi_z[n] - psi_z[n - e_y] - psi_y[n] + psi_y[n - e_z]) / h, and cyclically.
+ *   m            : one level (nlevels = 1); block_role is ignored: every block is a source and receives
+ *                  u.  The streamfunction is solved on the blocks and on their -x, -y, -z
+ *                  neighbour blocks, so the table's max_block_offset must cover the box extended by one
+ *                  block toward -x, -y and -z.
+ *   omega_dev    : device [3][nblocks][B^3] (x fastest) in dtype; read only.
+ *   u_dev        : device [3][nblocks][B^3] in dtype; every cell written.
+ *   opts, rep    : as for lgf_poisson_solve (the report is the streamfunction solve's, with the curl
+ *                  kernel added to kernel_launches).
+ * Scratch: the vorticity and the streamfunction on the extended block set, allocated and freed in
+ * stream order.  Errors: as lgf_poisson_solve; LGF_E_MESH for nlevels != 1; LGF_E_OOM for the scratch.
+ */
+int lgf_velocity_refresh(lgf_table *t, const lgf_mesh *m, const void *omega_dev, void *u_dev, int32_t dtype,
+                         const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream);
+
+/*
  * lgf_device_status -- synchronise the device and read the table's device status word: LGF_E_TIMEOUT
  * (and the word cleared) when a bounded device-side wait of a kernel that used this table gave up since
  * the last read, else LGF_OK.  Solves with opts->timing or opts->residual set read it themselves.

@@ -17,6 +17,7 @@ namespace lgf {
 
 int set_error(int code, const char *fmt, ...);
 int check_slices(const lgf_solve_opts &o);
+int check_mesh(const lgf_mesh *m, int B_expected);
 
 // Twiddles W_64^j from long-double cos/sin of the first octant and exact symmetries.
 template <class R>

@@ -81,6 +81,8 @@ def load():
                                        c_double, POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
         lib.lgf_poisson_solve_static.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p,
                                                  c_int32, c_int32, c_void_p]
+        lib.lgf_velocity_refresh.argtypes = [c_void_p, POINTER(lgf_mesh), c_void_p, c_void_p, c_int32,
+                                             POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
         PP = POINTER(c_void_p)
         lib.lgf_batch_create.argtypes = [POINTER(c_void_p), c_void_p, c_int32, POINTER(lgf_mesh), c_int32, c_int32,
                                          POINTER(c_double), POINTER(lgf_solve_opts), c_int32]
@@ -94,7 +96,8 @@ def load():
         lib.lgf_last_error.restype = c_char_p
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
-                     "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_batch_create", "lgf_batch_destroy",
+                     "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_velocity_refresh", "lgf_batch_create",
+                     "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
                      "lgf_device_status", "lgf_selftest_wait_timeout"):
             getattr(lib, name).restype = c_int32
@@ -184,6 +187,17 @@ def lgf_heat_apply(table, mesh: Mesh, ncomp: int, f_dev: int, g_dev: int, dtype:
                                  ctypes.byref(opts) if opts is not None else None,
                                  ctypes.byref(report) if report is not None else None,
                                  c_void_p(cuda_stream or None)))
+
+
+def lgf_velocity_refresh(table, mesh: Mesh, omega_dev: int, u_dev: int, dtype: int,
+                         opts: lgf_solve_opts | None = None, report: lgf_report | None = None,
+                         cuda_stream: int = 0) -> None:
+    """u = -C^T L_E^{-1} omega on one level: omega on the positive edges, u on the positive faces, both
+    [3][nblocks][B^3] device fields in dtype (Sec. 4.1, Eq. (eq:vel_update))."""
+    _check(load().lgf_velocity_refresh(c_void_p(table), ctypes.byref(mesh.c), c_void_p(omega_dev), c_void_p(u_dev),
+                                       int(dtype), ctypes.byref(opts) if opts is not None else None,
+                                       ctypes.byref(report) if report is not None else None,
+                                       c_void_p(cuda_stream or None)))
 
 
 def lgf_poisson_solve_static(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, dtype: int = LGF_F64,
