@@ -651,9 +651,9 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "pair", "box"])
     ap.add_argument("--batch", default=1, type=int,
                     help="also time the 64-instance batched RK3 stage and the composite-mesh heat apply (0: skip)")
-    ap.add_argument("--workload", default="ring", choices=["ring", "batch", "heat"],
+    ap.add_argument("--workload", default="ring", choices=["ring", "batch", "heat", "refresh"],
                     help="batch: only the 64-instance batched RK3 stage; heat: only the composite-mesh "
-                         "heat apply (each its own JSON line)")
+                         "heat apply; refresh: only the velocity refresh (each its own JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -662,6 +662,8 @@ def main():
         run_batch_only(args)
     elif args.workload == "heat":
         run_heat_only(args)
+    elif args.workload == "refresh":
+        run_refresh_only(args)
     else:
         run_gpu(args)
 
@@ -703,6 +705,27 @@ def run_heat_only(args):
                 "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "df32", "data": "synthetic", "config": out,
                 "roofline": out["roofline"], "e2e": out["e2e"], "gpu_launches": out["gpu_launches"] * args.steps}
+        print(json.dumps(line), flush=True)
+    _replicas_done(world)
+
+
+def run_refresh_only(args):
+    """The velocity refresh alone (one replica per rank), printed by rank 0."""
+    import torch
+    import paper_2010_13213_gb300.lgf as L
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _replicas_init(world, local)
+    case, _ = build_case()
+    out = refresh_line(L, torch, dev, case, args.steps, args.warmup)
+    ms = max_over_ranks([out["ms_per_step"]], world, dev)[0]
+    if rank == 0:
+        line = {"metric": "velocity refresh u = -C^T L_E^-1 omega, Mcells/s",
+                "value": replica_rate(int(np.prod(case["shape"])), ms, world), "unit": "Mcells/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "df32",
+                "data": "synthetic", "config": out, "gpu_launches": out["gpu_launches"] * args.steps}
         print(json.dumps(line), flush=True)
     _replicas_done(world)
 
