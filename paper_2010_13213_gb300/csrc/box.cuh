@@ -16,7 +16,7 @@
 //
 // The block-index DFTs have P = 2 nb points of which only nb inputs (forward) or outputs (inverse)
 // are used; they are evaluated directly by conjugate pairs (real coefficients cos, sin of 2 pi j k / P),
-// a CTA taking a chunk of pair slots (forward) or outputs (inverse); for nb <= 6 the block count is a
+// a CTA taking a chunk of pair slots (forward) or outputs (inverse); for nb <= 8 the block count is a
 // compile-time constant and one chunk covers the line.
 #pragma once
 #include "common.cuh"

@@ -174,36 +174,39 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
       return;
     }
     // one cell per thread: more resident warps to cover the loads (the passes are latency-bound)
-    // 2 <= nb <= 6: compile-time block counts (one chunk in both directions)
+    // 2 <= nb <= 8: compile-time block counts, one chunk in both directions (nb 7 and 8 with chunks of
+    // nb - 1 pair slots and nb outputs); wider boxes: runtime counts, chunks of CHF / CHI
     constexpr int NT = 128, CHF = 5, CHI = 6, REP = 1;
     static_assert(CHF + 1 >= 6 && CHI >= 6, "the nb <= 6 specialisations need one chunk");
     if (!inverse) {
-      const int nch = std::max(1, (nb_ax - 1 + CHF - 1) / CHF);  // general slots q = 1 .. nb - 1
-      const dim3 grid(B3 / (NT * REP), lines, n * nch);
-      auto go = [&](auto kern) {
-        kern<<<grid, NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, nch, sp);
+      auto go = [&](auto kern, int nch) {
+        kern<<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax),
+                                                                   gather, nch, sp);
       };
       switch (nb_ax) {
-        case 2: go(k_bdft_fwd<R, B, CHF, NT, REP, 2>); break;
-        case 3: go(k_bdft_fwd<R, B, CHF, NT, REP, 3>); break;
-        case 4: go(k_bdft_fwd<R, B, CHF, NT, REP, 4>); break;
-        case 5: go(k_bdft_fwd<R, B, CHF, NT, REP, 5>); break;
-        case 6: go(k_bdft_fwd<R, B, CHF, NT, REP, 6>); break;
-        default: go(k_bdft_fwd<R, B, CHF, NT, REP, 0>);
+        case 2: go(k_bdft_fwd<R, B, CHF, NT, REP, 2>, 1); break;
+        case 3: go(k_bdft_fwd<R, B, CHF, NT, REP, 3>, 1); break;
+        case 4: go(k_bdft_fwd<R, B, CHF, NT, REP, 4>, 1); break;
+        case 5: go(k_bdft_fwd<R, B, CHF, NT, REP, 5>, 1); break;
+        case 6: go(k_bdft_fwd<R, B, CHF, NT, REP, 6>, 1); break;
+        case 7: go(k_bdft_fwd<R, B, 6, NT, REP, 7>, 1); break;
+        case 8: go(k_bdft_fwd<R, B, 7, NT, REP, 8>, 1); break;
+        default: go(k_bdft_fwd<R, B, CHF, NT, REP, 0>, std::max(1, (nb_ax - 1 + CHF - 1) / CHF));
       }
     } else {
-      const int nch = (nout + CHI - 1) / CHI;
-      const dim3 grid(B3 / (NT * REP), lines, n * nch);
-      auto go = [&](auto kern) {
-        kern<<<grid, NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, nch, outs, sc);
+      auto go = [&](auto kern, int nch) {
+        kern<<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax),
+                                                                   final, nch, outs, sc);
       };
       switch (nb_ax) {
-        case 2: go(k_bdft_inv<R, B, CHI, NT, REP, 2>); break;
-        case 3: go(k_bdft_inv<R, B, CHI, NT, REP, 3>); break;
-        case 4: go(k_bdft_inv<R, B, CHI, NT, REP, 4>); break;
-        case 5: go(k_bdft_inv<R, B, CHI, NT, REP, 5>); break;
-        case 6: go(k_bdft_inv<R, B, CHI, NT, REP, 6>); break;
-        default: go(k_bdft_inv<R, B, CHI, NT, REP, 0>);
+        case 2: go(k_bdft_inv<R, B, CHI, NT, REP, 2>, 1); break;
+        case 3: go(k_bdft_inv<R, B, CHI, NT, REP, 3>, 1); break;
+        case 4: go(k_bdft_inv<R, B, CHI, NT, REP, 4>, 1); break;
+        case 5: go(k_bdft_inv<R, B, CHI, NT, REP, 5>, 1); break;
+        case 6: go(k_bdft_inv<R, B, CHI, NT, REP, 6>, 1); break;
+        case 7: go(k_bdft_inv<R, B, 7, NT, REP, 7>, 1); break;
+        case 8: go(k_bdft_inv<R, B, 8, NT, REP, 8>, 1); break;
+        default: go(k_bdft_inv<R, B, CHI, NT, REP, 0>, (nout + CHI - 1) / CHI);
       }
     }
   };
