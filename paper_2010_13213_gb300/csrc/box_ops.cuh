@@ -177,7 +177,7 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
     // 2 <= nb <= 8: compile-time block counts, one chunk in both directions (nb 7 and 8 with chunks of
     // nb - 1 pair slots and nb outputs); wider boxes: runtime counts, chunks of CHF / CHI
     constexpr int NT = 128, CHF = 5, CHI = 6, REP = 1;
-    static_assert(CHF + 1 >= 6 && CHI >= 6, "the nb <= 6 specialisations need one chunk");
+    static_assert(CHF + 1 >= 6 && CHI >= 6, "the nb <= 6 specialisations share the one-chunk sizes CHF, CHI");
     if (!inverse) {
       auto go = [&](auto kern, int nch) {
         kern<<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax),
