@@ -34,7 +34,11 @@ FIF-AMR (Sec. 3.5, Eq. (eq:FIF-AMR)): ``g_k = Gamma_k E_{alpha_k} * (P_k fhat)``
 
 Parity: K = 1 reduces to the single-level solve (pinned in ``core``); ``s_k = 0`` for linear psi;
 with n_ext -> infinity the result approaches the composite-grid definition
-``phi^k = L_k^{-1} sum_i P_{i->k} fhat_i`` evaluated directly (tests/test_oracle_amr.py).
+``phi^k = L_k^{-1} sum_i P_{i->k} fhat_i`` evaluated directly (tests/test_oracle_amr.py).  FIF-AMR
+equals the heat definition ``E_{alpha_k} * sum_i P_{i->k} fhat_i`` (P composed per source level) on
+two and three levels, and both reproduce the lattice heat kernel's second moment
+``E_a * |n|^2 = |n|^2 + 6a``: the same physical increment ``6 kappa dt`` on every level pins the
+``4^{-(K-1-k)}`` scaling of alpha_k.
 """
 from __future__ import annotations
 
@@ -45,8 +49,8 @@ import scipy.fft as sfft
 
 from . import core
 
-__all__ = ["Level", "build_levels", "flgf_amr", "fif_amr", "composite_definition", "interp_up",
-           "coarsen", "dilate_maxnorm", "laplacian_box", "solve_level_box"]
+__all__ = ["Level", "build_levels", "flgf_amr", "fif_amr", "composite_definition", "composite_heat_definition",
+           "interp_up", "coarsen", "dilate_maxnorm", "laplacian_box", "solve_level_box"]
 
 
 class Level:
@@ -288,6 +292,37 @@ def composite_definition(mesh, f_levels):
         phi = solve_level_box(tot, lv[k])
         p = np.where(lv[k].omega[None], phi, 0.0)
         out.append(_to_blocks(lv[k], blocks[k], p, B))
+    return out
+
+
+def composite_heat_definition(mesh, f_levels, alpha_finest):
+    """The composite-grid definition of the heat apply (Eqs. (eq:interp), (eq:FIF-AMR)):
+    ``g_k = E_{alpha_k} * (sum_i P_{i->k} fhat_i)`` restricted to Omega_k, every P applied to the whole
+    (compact) source of level i and composed level by level (Eq. (eq:P_composition)), the sum formed on
+    the full level box and convolved there (no region cut), ``alpha_k = alpha_finest 4^{-(K-1-k)}``
+    (Eq. (eq:composite-LGF-IF): the argument kappa dt / dx_k^2 on a level of spacing dx_k)."""
+    B = mesh["B"]
+    blocks = mesh["levels"]
+    K = len(blocks)
+    lv = build_levels(mesh, pad_extra=8)
+    fhat = [_user_field(lv[k], blocks[k], f_levels[k], B) for k in range(K)]
+    out = []
+    for k in range(K):
+        tot = fhat[k].copy()
+        for i in range(k):
+            u = fhat[i]
+            for j in range(i + 1, k + 1):
+                u = np.nan_to_num(interp_up(u, lv[j - 1], lv[j]), nan=0.0)
+            tot = tot + u
+        for i in range(k + 1, K):
+            u = fhat[i]
+            for j in range(i - 1, k - 1, -1):
+                u = coarsen(u, lv[j + 1], lv[j])
+            tot = tot + u
+        dx_ratio = 2.0 ** (K - 1 - k)  # dx_k / dx_finest
+        g = core.heat_box(tot, alpha_finest / dx_ratio ** 2)
+        g = np.where(lv[k].omega[None], g, 0.0)
+        out.append(_to_blocks(lv[k], blocks[k], g, B))
     return out
 
 

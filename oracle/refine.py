@@ -20,7 +20,9 @@ Readings (the paper states the criteria per point and the maximum per block, for
 
 Pins (tests/test_oracle_refine.py): block RMS against sums over the caller's input arrays (one level;
 two levels with no coarse source, where S_1 is the fine input and S_0 its 8-child mean), scale
-invariance of the flags, S_max carried over time, refine and coarsen never both set.
+invariance of the flags, S_max carried over time, refine and coarsen never both set, and the extended
+region flagging exactly the level-0 blocks under it (a mesh whose expected block set is written out in
+block coordinates).
 """
 import numpy as np
 

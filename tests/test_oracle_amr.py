@@ -142,3 +142,68 @@ def test_heat_preserves_constants_away_from_level_boundaries():
         box[(slice(None),) + lv[0].block_slice(b, B)] = g[0][:, i]
     assert deep.sum() > 100
     assert np.abs(box[0][deep] - 1.0).max() < 1e-14
+
+
+def _nested_mesh(B, shapes_and_offsets, h0=1.0, n_ext=4):
+    """Nested levels: level 0 tiles a box; level k >= 1 tiles a box of level-k blocks starting at the
+    given level-k block offset (every level-k block inside a level-(k-1) block)."""
+    levels = []
+    for k, (shape, off) in enumerate(shapes_and_offsets):
+        levels.append(S.box_blocks(shape, B) + np.asarray(off, np.int32))
+    return dict(B=B, h0=h0, n_ext=n_ext, levels=levels)
+
+
+def _centre_field(mesh, fn):
+    """fn(x, y, z) at every user cell centre of every level, x in level-0 spacing units."""
+    B = mesh["B"]
+    out = []
+    for k, blk in enumerate(mesh["levels"]):
+        h = mesh["h0"] / 2 ** k
+        data = np.zeros((1, len(blk), B, B, B))
+        for i, (bx, by, bz) in enumerate(blk):
+            z, y, x = np.meshgrid(*[(B * b + np.arange(B) + 0.5) * h for b in (bz, by, bx)], indexing="ij")
+            data[0, i] = fn(x, y, z)
+        out.append(data)
+    return out
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_heat_matches_composite_heat_definition(K):
+    # FIF-AMR's cumulative P_k fhat (coarsening F_k plus cumulative interpolation U_{k-1}) equals the
+    # per-source-level composed P_{i->k} of the definition (both linear), sources on every level
+    B = 8
+    spec = [((24, 24, 24), (0, 0, 0)), ((16, 16, 32), (1, 2, 1)), ((16, 16, 16), (3, 5, 3))][:K]
+    mesh = _nested_mesh(B, spec)
+    rng = np.random.default_rng(11 + K)
+    f = [rng.standard_normal((2, len(b), B, B, B)) for b in mesh["levels"]]
+    got = amr.fif_amr(mesh, f, 0.1)
+    want = amr.composite_heat_definition(mesh, f, 0.1)
+    lv = amr.build_levels(mesh)
+    for k in range(K):
+        om = amr._to_blocks(lv[k], mesh["levels"][k], lv[k].omega[None].astype(float), B)[0] > 0.5
+        assert om.any()
+        scale = np.abs(want[k][:, om]).max()
+        assert np.abs(got[k] - want[k])[:, om].max() <= 1e-14 * scale, k
+
+
+@pytest.mark.parametrize("which", ["fif_amr", "definition"])
+def test_heat_second_moment_gives_the_same_physical_increment_on_every_level(which):
+    # E_a * |n|^2 = |n|^2 + 6a on the unit lattice (zero mean, variance 2a per axis of the lattice heat
+    # kernel), so for q = |x - c|^2 in physical units E_{alpha_k} * q = q + 6 alpha_k h_k^2 on cells
+    # where the reconstruction P_k fhat is q itself.  One time step diffuses by the same kappa dt on
+    # every level: the increment must equal 6 alpha_finest h_finest^2 on each of them.
+    B = 8
+    mesh = _nested_mesh(B, [((64, 64, 64), (0, 0, 0)), ((48, 48, 48), (1, 1, 1))], h0=1.0, n_ext=4)
+    c = (32.0, 32.0, 32.0)
+    q = _centre_field(mesh, lambda x, y, z: (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    alpha = 0.1
+    g = amr.fif_amr(mesh, q, alpha) if which == "fif_amr" else amr.composite_heat_definition(mesh, q, alpha)
+    lv = amr.build_levels(mesh)
+    expected = 6.0 * alpha * (mesh["h0"] / 2) ** 2
+    for k in range(2):
+        r = len(core.heat_weights_1d(alpha / 4 ** (1 - k))) - 1
+        deep_box = lv[k].omega & ~amr.dilate_maxnorm(~lv[k].omega, r + 3)
+        deep = amr._to_blocks(lv[k], mesh["levels"][k], deep_box[None].astype(float), B)[0] > 0.5
+        assert deep.sum() > 200, k
+        inc = (g[k] - q[k])[0][deep]
+        assert np.abs(inc - expected).max() < 1e-10 * expected, (k, inc.min(), inc.max(), expected)

@@ -78,3 +78,26 @@ def test_smax_carried_over_time_raises_the_thresholds():
     for k in range(2):
         assert (later["refine"][k] <= now["refine"][k]).all()   # higher threshold: never more refinement
         assert (later["coarsen"][k] >= now["coarsen"][k]).all()
+
+
+def test_extended_region_flags_the_coarse_blocks_under_it():
+    # Level-0 blocks with no source of their own are flagged for refinement exactly when a level-1
+    # extended-region cell with a correction source above the level-1 threshold lies in them (Sec. 4.2:
+    # points of Omega_1^E outside the level-1 blocks).  The only source is a level-0 block far from
+    # level 1, so the correction s = (P L_0 - L_1 P) psi_0 is the whole of S_1; alpha = 0.01 with
+    # N_l = 5 puts the level-1 threshold at 1e-8 S_max, far below s on the extended region.
+    B = 8
+    lvl0 = S.box_blocks((48, 48, 48), B)                    # level-0 blocks 0..5 per axis
+    lvl1 = S.box_blocks((16, 16, 16), B) + np.int32(4)      # covers level-0 block (2, 2, 2) exactly
+    mesh = dict(B=B, h0=1.0, n_ext=8, levels=[lvl0, lvl1])  # N_E = 8 fine cells = 4 coarse cells < B
+    f0 = np.zeros((1, len(lvl0), B, B, B))
+    src = [i for i, b in enumerate(lvl0) if tuple(b) == (5, 5, 5)][0]
+    z, y, x = np.meshgrid(*[np.arange(B) - 3.5] * 3, indexing="ij")
+    f0[0, src] = np.exp(-(x ** 2 + y ** 2 + z ** 2) / 8.0)
+    f1 = np.zeros((1, len(lvl1), B, B, B))
+    out = refine.refinement_indicator(mesh, [f0, f1], 0.01, 0.5, 5)
+    want = {(5, 5, 5)}
+    want |= {(2 + dx, 2 + dy, 2 + dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)}
+    want.discard((2, 2, 2))  # covered by level 1: its own S_0 is the (zero) coarsened level-1 source
+    got = {tuple(int(v) for v in b) for b, r in zip(lvl0, out["refine"][0]) if r}
+    assert got == want
