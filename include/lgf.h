@@ -269,8 +269,10 @@ int lgf_batch_graph_nodes(const lgf_batch *b, int64_t *nodes);
  * Requests whose scratch (source and target spectra: ncomp x blocks x (2B)^2 (B+1) complex values,
  * plus index lists) exceeds 32 MiB fail with LGF_E_INVALID_ARG and a message giving the size.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array: calls whose GPU work may
- * overlap race on it and must be ordered by the caller.  It calls no cudaMalloc/cudaFree.
+ * first call before any stream capture.  Every call copies its block index lists from pageable host
+ * memory into the array; on a stream that is capturing, the call returns LGF_E_UNSUPPORTED before
+ * enqueueing anything, and a failed copy returns LGF_E_CUDA.  All calls share the array: calls whose
+ * GPU work may overlap race on it and must be ordered by the caller.  It calls no cudaMalloc/cudaFree.
  */
 int lgf_poisson_solve_static(const lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev,
                              void *phi_dev, int32_t dtype, int32_t precision, void *cuda_stream);

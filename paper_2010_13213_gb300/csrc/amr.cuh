@@ -230,6 +230,50 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, const int4 *blocks
   if (smax > 0.0) atomicMax(out + 1, (unsigned long long)__double_as_longlong(smax));
 }
 
+// Single-level FP64 residual; grid (ntgt, ncomp).  r = L phi - [source block] f at cells of target
+// blocks whose six neighbours lie in target blocks (tmap: block coords over the box lo + [0, n) ->
+// caller block index of a target block or -1; is_src: per caller block, 1 when it carries source
+// values).  out[0] = max |r|, out[1] = max |f| over the same cells (ordered uint64 bits).
+static __global__ void __launch_bounds__(256)
+    k_residual_single(const int32_t *tmap, int3 lo, int3 n, int shift, double h, const int32_t *tgt_idx,
+                      const int4 *tgt_c, const uint8_t *is_src, const void *phi, const void *f, int dtype, int64_t cs,
+                      unsigned long long *out) {
+  const int comp = blockIdx.y, B = 1 << shift, B3 = B * B * B, m = B - 1;
+  const int u0 = tgt_idx[blockIdx.x];
+  const int4 bc = tgt_c[blockIdx.x];
+  const double inv_h2 = 1.0 / (h * h);
+  double rmax = 0.0, smax = 0.0;
+  auto at = [&](int x, int y, int z, bool &ok) -> double {
+    const int bx = (x >> shift) - lo.x, by = (y >> shift) - lo.y, bz = (z >> shift) - lo.z;
+    if ((unsigned)bx >= (unsigned)n.x || (unsigned)by >= (unsigned)n.y || (unsigned)bz >= (unsigned)n.z) {
+      ok = false;
+      return 0.0;
+    }
+    const int u = tmap[((int64_t)bz * n.y + by) * n.x + bx];
+    if (u < 0) {
+      ok = false;
+      return 0.0;
+    }
+    const int off = (((z & m) << shift) + (y & m)) * B + (x & m);
+    return load_field<double>(phi, comp * cs + (int64_t)u * B3 + off, dtype);
+  };
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    const int x = (bc.x << shift) + (off & m), y = (bc.y << shift) + ((off >> shift) & m),
+              z = (bc.z << shift) + (off >> (2 * shift));
+    bool ok = true;
+    const double c0 = load_field<double>(phi, comp * cs + (int64_t)u0 * B3 + off, dtype);
+    const double s = at(x + 1, y, z, ok) + at(x - 1, y, z, ok) + at(x, y + 1, z, ok) + at(x, y - 1, z, ok) +
+                     at(x, y, z + 1, ok) + at(x, y, z - 1, ok);
+    if (!ok) continue;
+    const double src = is_src[u0] ? load_field<double>(f, comp * cs + (int64_t)u0 * B3 + off, dtype) : 0.0;
+    const double ar = fabs((s - 6.0 * c0) * inv_h2 - src);
+    rmax = (ar != ar) ? 1e300 : fmax(rmax, ar);
+    smax = fmax(smax, fabs(src));
+  }
+  if (rmax > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(rmax));
+  if (smax > 0.0) atomicMax(out + 1, (unsigned long long)__double_as_longlong(smax));
+}
+
 // ------------------------------------------------------------------ heat apply (FIF-AMR)
 struct HeatW {
   double w[65];  // w[n] = e^{-2 alpha} I_n(2 alpha), n <= r

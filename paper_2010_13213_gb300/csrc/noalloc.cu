@@ -11,7 +11,9 @@
 // LGF_STATIC_SCRATCH_BYTES until the process exits.  Host code cannot use the array's name as a
 // device address; the first call on each device looks the address up with cudaGetSymbolAddress
 // (with that device current) and caches it.  That first call should therefore happen before any
-// stream capture.  All calls share the one array: calls whose GPU work overlaps (different streams,
+// stream capture.  Every call copies its block index lists from pageable host memory into the array,
+// so a call on a stream that is capturing is rejected (LGF_E_UNSUPPORTED) before anything is
+// enqueued.  All calls share the one array: calls whose GPU work overlaps (different streams,
 // or different host threads without ordering) race on it and must be serialised by the caller.
 // Nothing in the array needs to start at zero: every byte a call reads was written earlier in the
 // same call.
@@ -114,12 +116,26 @@ static int solve_static(const lgf_table *t, const lgf_mesh *m, int ncomp, const 
   int32_t *d_tgt_idx = d_src_idx + nsrc;
   void *F = p + idx_bytes;
   void *P = p + idx_bytes + specF;
-  if (nsrc) {
-    cudaMemcpyAsync(d_src_c, src_c.data(), sizeof(int4) * nsrc, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(d_src_idx, src_idx.data(), sizeof(int32_t) * nsrc, cudaMemcpyHostToDevice, st);
+  // The index lists go up from pageable host vectors: the copy returns once the data is staged, so the
+  // vectors may be released when this function returns.
+  struct Up {
+    void *dst;
+    const void *src;
+    size_t n;
+    const char *what;
+  } ups[4] = {{d_src_c, src_c.data(), sizeof(int4) * nsrc, "source coordinates"},
+              {d_src_idx, src_idx.data(), sizeof(int32_t) * nsrc, "source indices"},
+              {d_tgt_c, tgt_c.data(), sizeof(int4) * ntgt, "target coordinates"},
+              {d_tgt_idx, tgt_idx.data(), sizeof(int32_t) * ntgt, "target indices"}};
+  for (const Up &u : ups) {
+    if (u.n == 0) continue;
+    const cudaError_t e = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(LGF_E_CUDA, "allocation-free solve: copy of the %s failed: %s", u.what,
+                       cudaGetErrorString(e));
+    }
   }
-  cudaMemcpyAsync(d_tgt_c, tgt_c.data(), sizeof(int4) * ntgt, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d_tgt_idx, tgt_idx.data(), sizeof(int32_t) * ntgt, cudaMemcpyHostToDevice, st);
   const int64_t cs = (int64_t)nb * B * B * B;
   if ((rc = PairOps<R>::forward(B, f, dtype, cs, d_src_idx, nsrc, ncomp, F, nullptr, 0, st))) return rc;
   if ((rc = PairOps<R>::mac(B, F, nsrc, (int64_t)nsrc * W, nullptr, d_src_c, Gh, t->mo, P, ntgt, (int64_t)ntgt * W,
@@ -148,6 +164,18 @@ extern "C" int lgf_poisson_solve_static(const lgf_table *t, const lgf_mesh *m, i
   if (!f_dev || !phi_dev || f_dev == phi_dev) return set_error(LGF_E_INVALID_ARG, "bad field pointers");
   if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // The index lists are copied from pageable host memory, which a capturing stream refuses (and the
+  // refusal would invalidate the caller's capture): reject before anything is enqueued.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LGF_E_CUDA, "allocation-free solve: cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(LGF_E_UNSUPPORTED,
+                     "allocation-free solve called on a capturing stream: its index lists are copied from "
+                     "pageable host memory, which stream capture does not accept");
   switch (precision) {
     case LGF_PREC_FP64: return solve_static<double>(t, m, ncomp, f_dev, phi_dev, dtype, st);
     case LGF_PREC_FP32: return solve_static<float>(t, m, ncomp, f_dev, phi_dev, dtype, st);

@@ -4,12 +4,15 @@
 // Every per-mesh list (source/target blocks, their coordinates, the box maps) lives in a cached
 // device-side plan, so a solve issues only kernel launches on its stream: it can be captured into a
 // CUDA graph once the plan, the kernel spectra and the workspace exist (an eager call creates them).
+#include <string.h>
+
 #include <algorithm>
 #include <cmath>
 #include <list>
 #include <string>
 #include <vector>
 
+#include "amr.cuh"
 #include "box_ops.cuh"
 #include "solver.h"
 
@@ -50,9 +53,15 @@ struct SinglePlan {
   int64_t nbox = 0;
   int32_t *d_idx = nullptr;      // src_idx [nsrc] | tgt_idx [ntgt] | box gather [nbox] | box scatter [nbox]
   int4 *d_c = nullptr;           // src coords [nsrc] | tgt coords [ntgt]
+  // residual: target-block map over the targets' block box (caller index or -1), source flag per block
+  int tlo[3] = {0, 0, 0}, tn[3] = {0, 0, 0};
+  int32_t *d_tmap = nullptr;
+  uint8_t *d_is_src = nullptr;
   ~SinglePlan() {
     cudaFree(d_idx);
     cudaFree(d_c);
+    cudaFree(d_tmap);
+    cudaFree(d_is_src);
   }
 };
 
@@ -127,14 +136,30 @@ static int single_plan(const lgf_mesh *m, SinglePlan **out) {
   }
   std::vector<int4> cs(src_c);
   cs.insert(cs.end(), tgt_c.begin(), tgt_c.end());
+  std::vector<int32_t> tmap;
+  std::vector<uint8_t> is_src(n, 0);
+  if (P->ntgt) {
+    int64_t nt = 1;
+    for (int a = 0; a < 3; ++a) P->tlo[a] = tlo[a], P->tn[a] = thi[a] - tlo[a] + 1, nt *= P->tn[a];
+    tmap.assign(nt, -1);
+    for (size_t j = 0; j < tgt_idx.size(); ++j) {
+      const int4 c = tgt_c[j];
+      tmap[((int64_t)(c.z - tlo[2]) * P->tn[1] + (c.y - tlo[1])) * P->tn[0] + (c.x - tlo[0])] = tgt_idx[j];
+    }
+  }
+  for (int i : src_idx) is_src[i] = 1;
   if (cudaMalloc(&P->d_idx, sizeof(int32_t) * std::max<size_t>(idx.size(), 1)) != cudaSuccess ||
-      cudaMalloc(&P->d_c, sizeof(int4) * std::max<size_t>(cs.size(), 1)) != cudaSuccess) {
+      cudaMalloc(&P->d_c, sizeof(int4) * std::max<size_t>(cs.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&P->d_tmap, sizeof(int32_t) * std::max<size_t>(tmap.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&P->d_is_src, std::max<size_t>(is_src.size(), 1)) != cudaSuccess) {
     cudaGetLastError();
     delete P;
     return set_error(LGF_E_OOM, "single-level plan allocation failed");
   }
   if (!idx.empty()) cudaMemcpy(P->d_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice);
   if (!cs.empty()) cudaMemcpy(P->d_c, cs.data(), sizeof(int4) * cs.size(), cudaMemcpyHostToDevice);
+  if (!tmap.empty()) cudaMemcpy(P->d_tmap, tmap.data(), sizeof(int32_t) * tmap.size(), cudaMemcpyHostToDevice);
+  if (!is_src.empty()) cudaMemcpy(P->d_is_src, is_src.data(), is_src.size(), cudaMemcpyHostToDevice);
   g_sp.emplace_front(key, P);
   while (g_sp.size() > 1024) {
     delete g_sp.back().second;
@@ -247,6 +272,40 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
   return LGF_OK;
 }
 
+// FP64 residual of a single-level solve (opts.residual): max |L phi - f| / max |f| over target cells
+// with six target neighbours; LGF_E_PRECISION above opts.residual_tol.  Synchronises the stream.
+static int single_residual(lgf_table *t, const lgf_mesh *m, const SinglePlan *P, int ncomp, const void *f,
+                           const void *phi, int dtype, const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  Workspace *ws = workspace_for(t, st);
+  int rc = ws->buf[15].reserve(sizeof(unsigned long long) * 2);
+  if (rc) return rc;
+  unsigned long long *racc = (unsigned long long *)ws->buf[15].p;
+  cudaMemsetAsync(racc, 0, sizeof(unsigned long long) * 2, st);
+  int shift = 0;
+  while ((1 << shift) < m->block) ++shift;
+  const int64_t cs = (int64_t)m->nblocks[0] * m->block * m->block * m->block;
+  k_residual_single<<<dim3(P->ntgt, ncomp), 256, 0, st>>>(
+      P->d_tmap, make_int3(P->tlo[0], P->tlo[1], P->tlo[2]), make_int3(P->tn[0], P->tn[1], P->tn[2]), shift, m->h0,
+      P->d_idx + P->nsrc, P->d_c + P->nsrc, P->d_is_src, phi, f, dtype, cs, racc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(LGF_E_CUDA, "residual launch: %s", cudaGetErrorString(e));
+  unsigned long long h[2] = {0, 0};
+  cudaMemcpyAsync(h, racc, sizeof h, cudaMemcpyDeviceToHost, st);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return set_error(LGF_E_CUDA, "residual failed: %s", cudaGetErrorString(e));
+  double r, s;
+  memcpy(&r, &h[0], 8);
+  memcpy(&s, &h[1], 8);
+  const double rel = s > 0 ? r / s : r;
+  if (rep) {
+    rep->residual_rel = rel;
+    rep->kernel_launches += 1;
+  }
+  if (o.residual_tol > 0 && rel > o.residual_tol)
+    return set_error(LGF_E_PRECISION, "FP64 residual %.3e exceeds the tolerance %.3e", rel, o.residual_tol);
+  return LGF_OK;
+}
+
 template <class R>
 static int solve_single_any(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
                             const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
@@ -262,9 +321,12 @@ static int solve_single_any(lgf_table *t, const lgf_mesh *m, int ncomp, const vo
                : LGF_MAC_PAIR;
   if (mode == LGF_MAC_BOX) {
     if (!P->box_ok) return set_error(LGF_E_UNSUPPORTED, "BOX mode needs 1..%d blocks per axis", BOX_NB_MAX);
-    return solve_single_box<R>(t, m, P, ncomp, f, phi, dtype, o, rep, st);
+    rc = solve_single_box<R>(t, m, P, ncomp, f, phi, dtype, o, rep, st);
+  } else {
+    rc = solve_single_pair<R>(t, m, P, ncomp, f, phi, dtype, o, rep, st);
   }
-  return solve_single_pair<R>(t, m, P, ncomp, f, phi, dtype, o, rep, st);
+  if (rc || !o.residual) return rc;
+  return single_residual(t, m, P, ncomp, f, phi, dtype, o, rep, st);
 }
 
 int solve_poisson(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,

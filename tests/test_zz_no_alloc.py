@@ -30,9 +30,9 @@ def _solve_pair(L, table, mesh, f, precision, dtype):
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (2, 1e-10)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (2, 1e-10), (1, 1e-5)])
 def test_static_matches_regular_on_two_calls(L, precision, tol):
-    table = L.lgf_table_create(16, (1, 1, 1), L.LGF_TBL_FP64 | L.LGF_TBL_DF32)
+    table = L.lgf_table_create(16, (1, 1, 1), L.LGF_TBL_FP64 | L.LGF_TBL_DF32 | L.LGF_TBL_FP32)
     try:
         case = S.single_level_random(n=32, B=16, seed=3, ncomp=2)
         mesh = L.Mesh([case["blocks"]], 16, case["h"])
@@ -65,5 +65,68 @@ def test_static_rejects_requests_beyond_its_scratch(L):
         with pytest.raises(L.LgfError) as e:
             L.lgf_poisson_solve_static(table, mesh, 3, f.data_ptr(), out.data_ptr(), L.LGF_F64, 0)
         assert e.value.status == L.LGF_E_INVALID_ARG and "static scratch" in str(e.value)
+    finally:
+        L.lgf_table_destroy(table)
+
+
+@pytest.mark.parametrize("roles", ["subset", "none"])
+def test_static_with_block_roles(L, roles):
+    # sources a strict subset of the targets (ragged source and target lists), or no source at all
+    # (every target block must then be written with zeros)
+    table = L.lgf_table_create(8, (3, 3, 3), L.LGF_TBL_FP64)
+    try:
+        case = S.single_level_random(n=32, B=8, seed=9, ncomp=2)
+        nb = len(case["blocks"])
+        role = np.full(nb, 2, np.uint8)
+        if roles == "subset":
+            role[::3] = 3
+            role[5] = 1  # a source that receives no output
+        mesh = L.Mesh([case["blocks"]], 8, case["h"], roles=role)
+        f = torch.from_numpy(case["f"]).cuda()
+        ref = _solve_pair(L, table, mesh, f, 0, L.LGF_F64)
+        for _ in range(2):
+            out = torch.full_like(f, float("nan"))
+            L.lgf_poisson_solve_static(table, mesh, 2, f.data_ptr(), out.data_ptr(), L.LGF_F64, 0)
+            torch.cuda.synchronize()
+            got, want = out.cpu().numpy(), ref.cpu().numpy()
+            tgt = (role & 2) > 0
+            assert np.isnan(got[:, ~tgt]).all()  # blocks without the target role are left untouched
+            if roles == "none":
+                assert (got[:, tgt] == 0.0).all()
+            else:
+                scale = np.abs(want[:, tgt]).max()
+                assert scale > 0 and np.abs(got[:, tgt] - want[:, tgt]).max() <= 1e-12 * scale
+    finally:
+        L.lgf_table_destroy(table)
+
+
+def test_static_refuses_a_capturing_stream(L):
+    # its index lists come from pageable host memory, which a capturing stream does not accept: the call
+    # must return LGF_E_UNSUPPORTED without touching the capture
+    table = L.lgf_table_create(16, (1, 1, 1), L.LGF_TBL_FP64)
+    try:
+        case = S.single_level_random(n=32, B=16, seed=4, ncomp=1)
+        mesh = L.Mesh([case["blocks"]], 16, case["h"])
+        f = torch.from_numpy(case["f"]).cuda()
+        out = torch.zeros_like(f)
+        L.lgf_poisson_solve_static(table, mesh, 1, f.data_ptr(), out.data_ptr(), L.LGF_F64, 0)  # set-up call
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        status = None
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            try:
+                L.lgf_poisson_solve_static(table, mesh, 1, f.data_ptr(), out.data_ptr(), L.LGF_F64, 0,
+                                           s.cuda_stream)
+            except L.LgfError as e:
+                status = e.status
+            out.add_(1.0)  # the capture is still valid: a later node records fine
+            g.capture_end()
+        assert status == L.LGF_E_UNSUPPORTED
+        before = out.clone()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, before + 1.0)
     finally:
         L.lgf_table_destroy(table)
