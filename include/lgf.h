@@ -118,6 +118,15 @@ typedef struct lgf_report {
   int64_t kernel_launches;/* kernels this call launched */
   int32_t mac_mode_used;  /* LGF_MAC_PAIR or LGF_MAC_BOX */
   int32_t reserved;
+  /* method-minimum work of the call, independent of how the kernels realise it (Poisson solves):
+   *   alg_bytes = sum over levels of ncomp (source cells + target cells) x (storage bytes of f, phi)
+   *               + the unique kernel-spectrum values the level needs x (bytes of a real in the arithmetic)
+   *               (block-index mode: the real spectrum of G is even in every axis, so (P_a B / 2 + 1) values
+   *               per axis are unique; pair mode: (2B)^2 (B+1) complex values per block offset used);
+   *   alg_flops = 5 M log2 M per complex FFT of M points (forward and inverse of every transformed field)
+   *               plus 8 flops per complex multiply-add of the pair sums. */
+  int64_t alg_bytes;
+  double alg_flops;
 } lgf_report;
 
 /*
@@ -205,6 +214,38 @@ int lgf_velocity_refresh(lgf_table *t, const lgf_mesh *m, const void *omega_dev,
                          const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream);
 
 /*
+ * lgf_refinement_indicator -- the Poisson solve of lgf_poisson_solve together with the refinement
+ * indicator of the adaptive mesh (Sec. 4.2, Eqs. (eq:refine1), (eq:maximumS), (eq:refine2)), reduced on
+ * the device from the combined source the solve builds anyway (Eq. (eq:combined_source)):
+ *   S_k = S psi_{k-1} + sum_{i >= k} P_{i->k} fhat_i   (the correction source on Omega_k and Omega_k^E plus
+ *         the level's own and the coarsened finer sources; S_0 = the cumulative source F_0),
+ *   |S_k| = Euclidean norm over the ncomp components,
+ *   rms   = sqrt(mean over the B^3 cells of a caller block of |S_k|^2),
+ *   S_max = max(previous S_max, largest block rms over all levels)               (Eq. (eq:maximumS)),
+ *   refine (bit 0)  : |S_k| > alpha^(N_l - k) S_max at a cell of the block        (Eq. (eq:refine1)), or at an
+ *                     Omega_{k+1}^E cell outside the level-(k+1) blocks that lies in this block,
+ *   coarsen (bit 1) : |S_k| < beta alpha^(N_l - k) S_max at every cell of the block (Eq. (eq:refine2)).
+ *   t, m, ncomp, f_dev, phi_dev, dtype, opts, rep : as for lgf_poisson_solve; every level (also a single
+ *                  one) runs the composite-mesh driver, so block_role is ignored.
+ *   ind          : host struct, read during the call; its three device pointers are written in stream
+ *                  order (s_max_dev is read first: pass 0 at the first step, then keep the value).
+ * Errors: as lgf_poisson_solve; LGF_E_INVALID_ARG for a NULL or out-of-range indicator field,
+ * LGF_E_UNSUPPORTED above 16 levels.
+ */
+typedef struct lgf_indicator {
+  double alpha;          /* 0 < alpha < 1 */
+  double beta;           /* 0 < beta < 1 */
+  int32_t n_levels_max;  /* N_l, the prescribed maximum level index (>= nlevels - 1) */
+  int32_t reserved;      /* 0 */
+  double *rms_dev;       /* device [sum nblocks]: block RMS of |S_k|, caller block order */
+  uint8_t *flags_dev;    /* device [sum nblocks]: bit 0 refine, bit 1 coarsen */
+  double *s_max_dev;     /* device [1], in/out: S_max carried over time */
+} lgf_indicator;
+int lgf_refinement_indicator(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev, void *phi_dev,
+                             int32_t dtype, const lgf_solve_opts *opts, const lgf_indicator *ind, lgf_report *rep,
+                             void *cuda_stream);
+
+/*
  * lgf_device_status -- synchronise the device and read the table's device status word: LGF_E_TIMEOUT
  * (and the word cleared) when a bounded device-side wait of a kernel that used this table gave up since
  * the last read, else LGF_OK.  Solves with opts->timing or opts->residual set read it themselves.
@@ -240,20 +281,26 @@ int lgf_batch_destroy(lgf_batch *b);
 /*
  * lgf_batch_stage -- for every instance i: phi_dev[i] = L^{-1} f_dev[i] and, when g_dev is non-NULL,
  * g_dev[i] = FIF-AMR heat apply of f_dev[i].  Device arrays laid out as for lgf_poisson_solve.
+ *   alpha : host [ninst] integrating-factor argument of this stage per instance, or NULL for the
+ *           values given at create time.  A HERK stage i uses (c~_i - c~_{i-1}) dt kappa / dx_finest^2
+ *           (Eq. (eq:composite-LGF-IF) with the tableau of Table tab:HREK), so it changes from stage to stage.
  * Work runs on the batch's streams, forked from and joined back into cuda_stream (asynchronous).
  */
 int lgf_batch_stage(lgf_batch *b, const void *const *f_dev, void *const *phi_dev, void *const *g_dev,
-                    void *cuda_stream);
+                    const double *alpha, void *cuda_stream);
 
 /*
- * lgf_batch_graph_create -- run two eager stages (building every plan, spectrum and workspace), then
- * capture `nstages` chained stages into a CUDA graph: stage 0 reads f and writes g, stage s >= 1 reads
- * the previous stage's heat output (g or tmp, alternating) and writes the other; every stage writes
- * phi.  cuda_stream must be a non-default stream.  Synchronises.  lgf_batch_graph_launch replays it
- * with one cudaGraphLaunch; lgf_batch_graph_nodes returns its node count.
+ * lgf_batch_graph_create -- run the stages once eagerly (building every plan, spectrum and workspace),
+ * then capture `nstages` chained stages into a CUDA graph.  With g_dev non-NULL: stage 0 reads f and
+ * writes g, stage s >= 1 reads the previous stage's heat output (g or tmp, alternating) and writes the
+ * other; every stage writes phi.  With g_dev NULL every stage is the Poisson solve phi = L^{-1} f alone
+ * (tmp_dev unused).  alpha_stages: host [nstages][ninst] per-stage integrating-factor arguments, or NULL
+ * for the create-time values.  cuda_stream must be a non-default stream.  Synchronises.
+ * lgf_batch_graph_launch replays it with one cudaGraphLaunch; lgf_batch_graph_nodes returns its node count.
  */
 int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_dev, void *const *phi_dev,
-                           void *const *g_dev, void *const *tmp_dev, void *cuda_stream);
+                           void *const *g_dev, void *const *tmp_dev, const double *alpha_stages,
+                           void *cuda_stream);
 int lgf_batch_graph_launch(lgf_batch *b, void *cuda_stream);
 int lgf_batch_graph_nodes(const lgf_batch *b, int64_t *nodes);
 

@@ -238,6 +238,32 @@ int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void
   return solve_poisson(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream);
 }
 
+int lgf_refinement_indicator(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev, void *phi_dev,
+                             int32_t dtype, const lgf_solve_opts *opts, const lgf_indicator *ind, lgf_report *rep,
+                             void *cuda_stream) {
+  if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");
+  int rc = check_mesh(m, t->B);
+  if (rc) return rc;
+  if (ncomp < 1) return set_error(LGF_E_INVALID_ARG, "ncomp %d", ncomp);
+  if (!f_dev || !phi_dev) return set_error(LGF_E_INVALID_ARG, "field pointer NULL");
+  if (f_dev == phi_dev) return set_error(LGF_E_INVALID_ARG, "f and phi alias");
+  if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
+  if (!ind || !ind->rms_dev || !ind->flags_dev || !ind->s_max_dev)
+    return set_error(LGF_E_INVALID_ARG, "indicator request or one of its device pointers is NULL");
+  if (!(ind->alpha > 0.0 && ind->alpha < 1.0) || !(ind->beta > 0.0 && ind->beta < 1.0))
+    return set_error(LGF_E_INVALID_ARG, "indicator alpha %g / beta %g outside (0, 1)", ind->alpha, ind->beta);
+  if (ind->n_levels_max < m->nlevels - 1 || ind->n_levels_max > 64)
+    return set_error(LGF_E_INVALID_ARG, "n_levels_max %d below the mesh's top level %d", ind->n_levels_max,
+                     m->nlevels - 1);
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0, 0, 0};
+  if (opts) o = *opts;
+  if (o.precision < 0 || o.precision > 2) return set_error(LGF_E_INVALID_ARG, "precision %d", o.precision);
+  if (o.mac_mode < 0 || o.mac_mode > 2) return set_error(LGF_E_INVALID_ARG, "mac_mode %d", o.mac_mode);
+  if ((rc = check_slices(o))) return rc;
+  if (rep) memset(rep, 0, sizeof(*rep));
+  return solve_multi(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream, ind);
+}
+
 int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev, void *g_dev,
                    int32_t dtype, double alpha_finest, const lgf_solve_opts *opts, lgf_report *rep,
                    void *cuda_stream) {

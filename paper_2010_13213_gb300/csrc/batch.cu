@@ -42,7 +42,8 @@ double box_cost(int B, const int nb[3]);
 
 using namespace lgf;
 
-static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, void *const *g, cudaStream_t st) {
+static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, void *const *g, const double *alpha,
+                       cudaStream_t st) {
   if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return set_error(LGF_E_CUDA, "batch fork event failed");
   for (int s = 0; s < b->nstreams; ++s) {
     cudaStream_t ss = b->streams[s];
@@ -51,7 +52,8 @@ static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, voi
       int rc = lgf_poisson_solve(b->t, &b->mesh[i], b->ncomp, f[i], phi[i], b->dtype, &b->opts, nullptr, ss);
       if (rc) return rc;
       if (g && g[i]) {
-        rc = lgf_heat_apply(b->t, &b->mesh[i], b->ncomp, f[i], g[i], b->dtype, b->alpha[i], &b->opts, nullptr, ss);
+        rc = lgf_heat_apply(b->t, &b->mesh[i], b->ncomp, f[i], g[i], b->dtype, alpha ? alpha[i] : b->alpha[i],
+                            &b->opts, nullptr, ss);
         if (rc) return rc;
       }
     }
@@ -142,40 +144,46 @@ int lgf_batch_destroy(lgf_batch *b) {
 }
 
 int lgf_batch_stage(lgf_batch *b, const void *const *f_dev, void *const *phi_dev, void *const *g_dev,
-                    void *cuda_stream) {
+                    const double *alpha, void *cuda_stream) {
   if (!b || !f_dev || !phi_dev) return set_error(LGF_E_INVALID_ARG, "NULL argument");
-  int rc = batch_stage(b, f_dev, phi_dev, g_dev, (cudaStream_t)cuda_stream);
+  int rc = batch_stage(b, f_dev, phi_dev, g_dev, alpha, (cudaStream_t)cuda_stream);
   if (!rc) b->warmed = true;
   return rc;
 }
 
 int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_dev, void *const *phi_dev,
-                           void *const *g_dev, void *const *tmp_dev, void *cuda_stream) {
-  if (!b || !f_dev || !phi_dev || !g_dev || nstages < 1) return set_error(LGF_E_INVALID_ARG, "NULL argument");
-  if (nstages > 1 && !tmp_dev) return set_error(LGF_E_INVALID_ARG, "chained stages need tmp buffers");
+                           void *const *g_dev, void *const *tmp_dev, const double *alpha_stages,
+                           void *cuda_stream) {
+  if (!b || !f_dev || !phi_dev || nstages < 1) return set_error(LGF_E_INVALID_ARG, "NULL argument");
+  const bool heat = g_dev != nullptr;
+  if (heat && nstages > 1 && !tmp_dev) return set_error(LGF_E_INVALID_ARG, "chained stages need tmp buffers");
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  // an eager stage creates every plan, spectrum and workspace the captured stages will use
+  auto alpha_of = [&](int s) { return alpha_stages ? alpha_stages + (size_t)s * b->n : nullptr; };
   std::vector<const void *> src(b->n);
   std::vector<void *> dst(b->n);
-  for (int i = 0; i < b->n; ++i) src[i] = f_dev[i], dst[i] = g_dev[i];
-  int rc = batch_stage(b, src.data(), phi_dev, dst.data(), st);
-  if (rc) return rc;
-  if (nstages > 1) {
-    for (int i = 0; i < b->n; ++i) src[i] = g_dev[i], dst[i] = tmp_dev[i];
-    if ((rc = batch_stage(b, src.data(), phi_dev, dst.data(), st))) return rc;
+  auto buffers_of = [&](int s) {
+    for (int i = 0; i < b->n; ++i) {
+      if (!heat || s == 0) src[i] = f_dev[i], dst[i] = heat ? g_dev[i] : nullptr;
+      else if (s % 2 == 1) src[i] = g_dev[i], dst[i] = tmp_dev[i];
+      else src[i] = tmp_dev[i], dst[i] = g_dev[i];
+    }
+  };
+  // every stage once eagerly: builds each plan (the heat plans depend on the stage's alpha), spectrum and
+  // workspace the captured stages use, so nothing allocates during the capture
+  int rc = LGF_OK;
+  for (int s = 0; s < nstages && !rc; ++s) {
+    buffers_of(s);
+    rc = batch_stage(b, src.data(), phi_dev, heat ? dst.data() : nullptr, alpha_of(s), st);
   }
+  if (rc) return rc;
   if (cudaStreamSynchronize(st) != cudaSuccess) return set_error(LGF_E_CUDA, "batch warm-up failed");
   if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
   if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return set_error(LGF_E_CUDA, "stream capture could not begin (use a non-default stream)");
   for (int s = 0; s < nstages && !rc; ++s) {
-    for (int i = 0; i < b->n; ++i) {
-      if (s == 0) src[i] = f_dev[i], dst[i] = g_dev[i];
-      else if (s % 2 == 1) src[i] = g_dev[i], dst[i] = tmp_dev[i];
-      else src[i] = tmp_dev[i], dst[i] = g_dev[i];
-    }
-    rc = batch_stage(b, src.data(), phi_dev, dst.data(), st);
+    buffers_of(s);
+    rc = batch_stage(b, src.data(), phi_dev, heat ? dst.data() : nullptr, alpha_of(s), st);
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(st, &graph);

@@ -149,7 +149,7 @@ struct DevBuf {
 
 // Per-stream scratch held by a table.
 struct Workspace {
-  DevBuf buf[16];
+  DevBuf buf[24];
   size_t total() const {
     size_t s = 0;
     for (auto &b : buf) s += b.bytes;

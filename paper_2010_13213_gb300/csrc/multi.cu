@@ -15,12 +15,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <list>
 #include <string>
 #include <vector>
 
 #include "amr.cuh"
 #include "box_ops.cuh"
+#include "indicator.cuh"
 #include "plan.h"
 #include "solver.h"
 
@@ -133,11 +135,13 @@ static int check_range(const Plan *P, const lgf_table *t) {
 
 template <class R>
 static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
-                         const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+                         const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st, const lgf_indicator *ind) {
   Plan *P = nullptr;
   int rc = get_plan(m, nullptr, &P);
   if (rc) return rc;
   if ((rc = check_range(P, t))) return rc;
+  if (ind && P->K > LGF_IND_MAX_LEVELS)
+    return set_error(LGF_E_UNSUPPORTED, "refinement indicator on more than %d levels", LGF_IND_MAX_LEVELS);
   const void *Gh = spectra_for<R>(t);  // null for a box-only table: every level then runs in box mode
   const int B = P->B, K = P->K;
   const int64_t B3 = (int64_t)B * B * B;
@@ -194,6 +198,13 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
   R *Psi = (R *)ws->buf[7].p;  // psi_k of every level, [level][ncomp][nBL_k][B^3]
   R *Lpsi = (R *)ws->buf[8].p;  // L_{k-1} psi_{k-1} of the current coarse level
   unsigned long long *racc = (unsigned long long *)ws->buf[9].p;
+  // refinement indicator: per level and internal block the sum of |S_k|^2 and max |S_k|
+  std::vector<int64_t> ind_off(K + 1, 0);
+  for (int k = 0; k < K; ++k) ind_off[k + 1] = ind_off[k] + (int64_t)P->L[k].BL.size();
+  if (ind && ((rc = ws->buf[16].reserve(sizeof(double) * 2 * (size_t)std::max<int64_t>(ind_off[K], 1))) ||
+              (rc = ws->buf[17].reserve(sizeof(int) * (size_t)std::max<int64_t>(total_user, 1)))))
+    return rc;
+  double *ind_ss = ind ? (double *)ws->buf[16].p : nullptr, *ind_mx = ind ? ind_ss + ind_off[K] : nullptr;
   int64_t launches = 0;
   PhaseTimer tm;
   tm.start(o.timing != 0, st);
@@ -238,6 +249,11 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
                                                      Lpsi, ccs, k > 0);
       LGF_LAUNCH_CHECK("correct");
       tm.mark(PH_CORRECT);
+    }
+    if (ind && !L.BL.empty()) {  // the combined source S_k = A_k + [covered] F_k, before A is reused
+      k_ind_stats<R><<<(unsigned)L.BL.size(), 256, 0, st>>>(Ld, L.nU, ncomp, A, Fall + Foff[k], cs[k],
+                                                             ind_ss + ind_off[k], ind_mx + ind_off[k]);
+      LGF_LAUNCH_CHECK("indicator statistics");
     }
     if (use_box[k]) {
       BoxSpec *S = nullptr;
@@ -346,6 +362,21 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     nsrc_total += nSA + nSB;
     ntgt_total += nT;
   }
+  if (ind) {
+    IndArgs a{};
+    a.K = K;
+    a.B3 = (int)B3;
+    a.nlmax = ind->n_levels_max;
+    a.alpha = ind->alpha;
+    a.beta = ind->beta;
+    for (int k = 0; k < K; ++k) {
+      const LevelPlan &L = P->L[k];
+      a.lv[k] = IndLevel{level_dev(P, k, m->h0), L.d_BL, (int)L.BL.size(), L.nU, L.user_off,
+                         ind_ss + ind_off[k], ind_mx + ind_off[k]};
+    }
+    k_ind_flags<<<1, 1024, 0, st>>>(a, ind->rms_dev, ind->flags_dev, ind->s_max_dev, (int *)ws->buf[17].p);
+    LGF_LAUNCH_CHECK("indicator flags");
+  }
   // 3. residual
   double resid = 0.0;
   if (o.residual) {
@@ -383,6 +414,39 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     rep->mac_mode_used = LGF_MAC_PAIR;
     for (int k = 0; k < K; ++k)
       if (use_box[k]) rep->mac_mode_used = LGF_MAC_BOX;
+    // method-minimum work (see lgf_report): per level the source cells (Omega_k, Omega_k^E and covered
+    // cells) read and the target cells (Omega_k and the psi targets) written once per component, the
+    // unique spectrum values, and the transforms / pair sums of the level's evaluation
+    const double w = dtype == LGF_F32 ? 4.0 : 8.0, W2 = (2.0 * B) * (2.0 * B) * (B + 1.0);
+    double bytes = 0.0, flops = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const LevelPlan &L = P->L[k];
+      if (L.Tall.empty()) continue;
+      const double tgt = (double)L.n_omega + (double)L.Tpsi.size() * B3;
+      bytes += ncomp * ((double)L.n_src + tgt) * w;
+      const bool packAB = !L.Tpsi.empty() || !L.SB.empty();
+      if (use_box[k]) {
+        double uniq = 1.0, M = 1.0;
+        for (int a = 0; a < 3; ++a) uniq *= L.box_nb[a] * B + 1.0, M *= 2.0 * L.box_nb[a] * B;
+        bytes += uniq * sizeof(R);
+        flops += 2.0 * (packAB ? ncomp : (ncomp + 1) / 2) * 5.0 * M * std::log2(M);
+      } else {
+        int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+        for (const auto &lst : {L.SA, L.SB, L.Tall})
+          for (int b : lst) {
+            const int v[3] = {L.BL[b].x, L.BL[b].y, L.BL[b].z};
+            for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], v[a]), hi[a] = std::max(hi[a], v[a]);
+          }
+        double noff = 1.0;
+        for (int a = 0; a < 3; ++a) noff *= 2.0 * (hi[a] - lo[a]) + 1.0;
+        bytes += noff * W2 * 2.0 * sizeof(R);
+        const double m = 8.0 * B3;
+        flops += ((double)L.SA.size() + L.SB.size() + L.nTall) * ncomp * 0.5 * 5.0 * m * std::log2(m) +
+                 8.0 * W2 * ncomp * ((double)L.SA.size() * L.nTall + (double)L.SB.size() * L.Tphi.size());
+      }
+    }
+    rep->alg_bytes = (int64_t)bytes;
+    rep->alg_flops = flops;
   }
   if (o.timing || o.residual) {
     cudaError_t e = cudaStreamSynchronize(st);
@@ -395,11 +459,11 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
 }
 
 int solve_multi(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
-                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st, const lgf_indicator *ind) {
   switch (o.precision) {
-    case LGF_PREC_FP64: return solve_multi_t<double>(t, m, ncomp, f, phi, dtype, o, rep, st);
-    case LGF_PREC_FP32: return solve_multi_t<float>(t, m, ncomp, f, phi, dtype, o, rep, st);
-    default: return solve_multi_t<df>(t, m, ncomp, f, phi, dtype, o, rep, st);
+    case LGF_PREC_FP64: return solve_multi_t<double>(t, m, ncomp, f, phi, dtype, o, rep, st, ind);
+    case LGF_PREC_FP32: return solve_multi_t<float>(t, m, ncomp, f, phi, dtype, o, rep, st, ind);
+    default: return solve_multi_t<df>(t, m, ncomp, f, phi, dtype, o, rep, st, ind);
   }
 }
 

@@ -307,6 +307,7 @@ int build_plan(const lgf_mesh *m, const int *heat_radii, Plan **out) {
             if (g & G_COV) cb |= CB_COV;
             L.cellmask[(size_t)i * B3 + ((size_t)z * B + y) * B + x] = cb;
             if ((cb & CB_OM) && i < L.nU) ++L.n_omega;
+            if (cb & (CB_OM | CB_EX | CB_COV)) ++L.n_src;
           }
     }
     // Tall = Tphi then (Tpsi minus Tphi); psi rows

@@ -49,6 +49,7 @@ struct LevelPlan {
   int off_SA = 0, off_SB = 0, off_Tall = 0, off_psi = 0, off_Tpsi = 0, off_HB = 0;
   int heat_r = 0;                  // heat kernel radius at this level
   int64_t n_omega = 0;             // |Omega_k| in cells
+  int64_t n_src = 0;               // cells carrying a source of the level's convolutions (OM, EX or COV)
   // block-index FFT mode: box over SA u SB u Tall and its maps (box block -> BL index or -1)
   bool box_ok = false;
   int box_lo[3] = {0, 0, 0}, box_nb[3] = {0, 0, 0};

@@ -19,7 +19,7 @@
 namespace lgf {
 
 int solve_multi(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
-                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st);
+                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st, const lgf_indicator *ind);
 
 template <class R>
 static const void *spectra_of(const lgf_table *t);
@@ -169,6 +169,29 @@ static int single_plan(const lgf_mesh *m, SinglePlan **out) {
   return LGF_OK;
 }
 
+// Method-minimum work of a single-level solve (see lgf_report): caller fields read and written once, the
+// unique kernel-spectrum values, 5 M log2 M per complex transform and 8 flops per pair multiply-add.
+static void alg_work_single(lgf_report *rep, const SinglePlan *P, int B, int ncomp, int dtype, size_t rsize,
+                            int mode) {
+  const double B3 = (double)B * B * B, W = (2.0 * B) * (2.0 * B) * (B + 1.0);
+  const double w = dtype == LGF_F32 ? 4.0 : 8.0;
+  double bytes = ncomp * (P->nsrc + P->ntgt) * B3 * w, flops = 0.0;
+  if (mode == LGF_MAC_BOX) {
+    double uniq = 1.0, M = 1.0;
+    for (int a = 0; a < 3; ++a) uniq *= P->nb[a] * B + 1.0, M *= 2.0 * P->nb[a] * B;
+    bytes += uniq * rsize;
+    flops = 2.0 * ((ncomp + 1) / 2) * 5.0 * M * std::log2(M);
+  } else {
+    double noff = 1.0;
+    for (int a = 0; a < 3; ++a) noff *= 2.0 * P->reach[a] + 1.0;
+    bytes += noff * W * 2.0 * rsize;
+    const double m = 8.0 * B3;
+    flops = (P->nsrc + P->ntgt) * 0.5 * ncomp * 5.0 * m * std::log2(m) + 8.0 * W * P->nsrc * P->ntgt * ncomp;
+  }
+  rep->alg_bytes = (int64_t)bytes;
+  rep->alg_flops = flops;
+}
+
 static void fill_report(lgf_report *rep, const SinglePlan *P, int64_t B3, const Workspace *ws, int64_t launches,
                         int mode, int64_t extra_bytes) {
   if (!rep) return;
@@ -218,6 +241,7 @@ static int solve_single_pair(lgf_table *t, const lgf_mesh *m, const SinglePlan *
   tm.mark(PH_INVERSE);
   tm.finish(rep);
   fill_report(rep, P, B3, ws, 2 + (ncomp + 2) / 3, LGF_MAC_PAIR, 0);
+  if (rep) alg_work_single(rep, P, B, ncomp, dtype, sizeof(R), LGF_MAC_PAIR);
   if (o.timing) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(LGF_E_CUDA, "solve failed: %s", cudaGetErrorString(e));
@@ -264,6 +288,7 @@ static int solve_single_box(lgf_table *t, const lgf_mesh *m, const SinglePlan *P
     return rc;
   tm.finish(rep);
   fill_report(rep, P, B3, ws, launches, LGF_MAC_BOX, (int64_t)S->bytes);
+  if (rep) alg_work_single(rep, P, B, ncomp, dtype, sizeof(R), LGF_MAC_BOX);
   if (o.timing) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(LGF_E_CUDA, "solve failed: %s", cudaGetErrorString(e));
@@ -331,7 +356,7 @@ static int solve_single_any(lgf_table *t, const lgf_mesh *m, int ncomp, const vo
 
 int solve_poisson(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
                   const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
-  if (m->nlevels > 1) return solve_multi(t, m, ncomp, f, phi, dtype, o, rep, st);
+  if (m->nlevels > 1) return solve_multi(t, m, ncomp, f, phi, dtype, o, rep, st, nullptr);
   switch (o.precision) {
     case LGF_PREC_FP64: return solve_single_any<double>(t, m, ncomp, f, phi, dtype, o, rep, st);
     case LGF_PREC_FP32: return solve_single_any<float>(t, m, ncomp, f, phi, dtype, o, rep, st);

@@ -8,6 +8,8 @@ Workspace *workspace_for(lgf_table *t, cudaStream_t st);
 
 int solve_poisson(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
                   const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st);
+int solve_multi(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
+                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st, const lgf_indicator *ind);
 int solve_heat(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype,
                double alpha_finest, const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st);
 

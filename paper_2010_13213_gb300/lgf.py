@@ -53,12 +53,17 @@ class lgf_report(ctypes.Structure):
     _fields_ = [("ms_total", c_double), ("ms_phase", c_double * 8), ("residual_rel", c_double),
                 ("target_cells", c_int64), ("source_blocks", c_int64), ("target_blocks", c_int64),
                 ("pairs", c_int64), ("scratch_bytes", c_int64), ("kernel_launches", c_int64),
-                ("mac_mode_used", c_int32), ("reserved", c_int32)]
+                ("mac_mode_used", c_int32), ("reserved", c_int32), ("alg_bytes", c_int64), ("alg_flops", c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("ms_phase", "reserved")}
         d["ms_phase"] = {p: self.ms_phase[i] for i, p in enumerate(PHASES)}
         return d
+
+
+class lgf_indicator(ctypes.Structure):
+    _fields_ = [("alpha", c_double), ("beta", c_double), ("n_levels_max", c_int32), ("reserved", c_int32),
+                ("rms_dev", c_void_p), ("flags_dev", c_void_p), ("s_max_dev", c_void_p)]
 
 
 _LIB = None
@@ -83,12 +88,15 @@ def load():
                                                  c_int32, c_int32, c_void_p]
         lib.lgf_velocity_refresh.argtypes = [c_void_p, POINTER(lgf_mesh), c_void_p, c_void_p, c_int32,
                                              POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
+        lib.lgf_refinement_indicator.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p, c_int32,
+                                                 POINTER(lgf_solve_opts), POINTER(lgf_indicator),
+                                                 POINTER(lgf_report), c_void_p]
         PP = POINTER(c_void_p)
         lib.lgf_batch_create.argtypes = [POINTER(c_void_p), c_void_p, c_int32, POINTER(lgf_mesh), c_int32, c_int32,
                                          POINTER(c_double), POINTER(lgf_solve_opts), c_int32]
         lib.lgf_batch_destroy.argtypes = [c_void_p]
-        lib.lgf_batch_stage.argtypes = [c_void_p, PP, PP, PP, c_void_p]
-        lib.lgf_batch_graph_create.argtypes = [c_void_p, c_int32, PP, PP, PP, PP, c_void_p]
+        lib.lgf_batch_stage.argtypes = [c_void_p, PP, PP, PP, POINTER(c_double), c_void_p]
+        lib.lgf_batch_graph_create.argtypes = [c_void_p, c_int32, PP, PP, PP, PP, POINTER(c_double), c_void_p]
         lib.lgf_batch_graph_launch.argtypes = [c_void_p, c_void_p]
         lib.lgf_batch_graph_nodes.argtypes = [c_void_p, POINTER(c_int64)]
         lib.lgf_device_status.argtypes = [c_void_p]
@@ -96,7 +104,8 @@ def load():
         lib.lgf_last_error.restype = c_char_p
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
-                     "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_velocity_refresh", "lgf_batch_create",
+                     "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_velocity_refresh",
+                     "lgf_refinement_indicator", "lgf_batch_create",
                      "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
                      "lgf_device_status", "lgf_selftest_wait_timeout"):
@@ -179,6 +188,20 @@ def lgf_poisson_solve(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, d
                                     c_void_p(cuda_stream or None)))
 
 
+def lgf_refinement_indicator(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev: int, dtype: int,
+                             opts: lgf_solve_opts | None, alpha: float, beta: float, n_levels_max: int,
+                             rms_dev: int, flags_dev: int, s_max_dev: int, report: lgf_report | None = None,
+                             cuda_stream: int = 0) -> None:
+    """Poisson solve plus the refinement indicator; rms_dev / flags_dev / s_max_dev are device addresses."""
+    ind = lgf_indicator(float(alpha), float(beta), int(n_levels_max), 0, c_void_p(rms_dev), c_void_p(flags_dev),
+                        c_void_p(s_max_dev))
+    _check(load().lgf_refinement_indicator(c_void_p(table), ctypes.byref(mesh.c), int(ncomp), c_void_p(f_dev),
+                                           c_void_p(phi_dev), int(dtype),
+                                           ctypes.byref(opts) if opts is not None else None, ctypes.byref(ind),
+                                           ctypes.byref(report) if report is not None else None,
+                                           c_void_p(cuda_stream or None)))
+
+
 def lgf_heat_apply(table, mesh: Mesh, ncomp: int, f_dev: int, g_dev: int, dtype: int, alpha_finest: float,
                    opts: lgf_solve_opts | None = None, report: lgf_report | None = None,
                    cuda_stream: int = 0) -> None:
@@ -226,18 +249,25 @@ class Batch:
                                        int(nstreams)))
         self.h = h.value
 
-    def stage(self, f_ptrs, phi_ptrs, g_ptrs=None, cuda_stream: int = 0):
+    def stage(self, f_ptrs, phi_ptrs, g_ptrs=None, cuda_stream: int = 0, alpha=None):
+        """alpha: per-instance integrating-factor arguments of this stage (None: the create-time values)."""
         f, _a = _ptrs(f_ptrs)
         p, _b = _ptrs(phi_ptrs)
         g, _c = _ptrs(g_ptrs) if g_ptrs is not None else (None, None)
-        _check(load().lgf_batch_stage(c_void_p(self.h), f, p, g, c_void_p(cuda_stream or None)))
+        al = None if alpha is None else (c_double * len(self.meshes))(*[float(a) for a in alpha])
+        _check(load().lgf_batch_stage(c_void_p(self.h), f, p, g, al, c_void_p(cuda_stream or None)))
 
-    def graph_create(self, nstages, f_ptrs, phi_ptrs, g_ptrs, tmp_ptrs, cuda_stream: int):
+    def graph_create(self, nstages, f_ptrs, phi_ptrs, g_ptrs, tmp_ptrs, cuda_stream: int, alpha_stages=None):
+        """g_ptrs None: Poisson-only stages.  alpha_stages: [nstages][ninst] values, or None."""
         f, _a = _ptrs(f_ptrs)
         p, _b = _ptrs(phi_ptrs)
-        g, _c = _ptrs(g_ptrs)
+        g, _c = _ptrs(g_ptrs) if g_ptrs is not None else (None, None)
         t, _d = _ptrs(tmp_ptrs) if tmp_ptrs is not None else (None, None)
-        _check(load().lgf_batch_graph_create(c_void_p(self.h), int(nstages), f, p, g, t, c_void_p(cuda_stream)))
+        al = None
+        if alpha_stages is not None:
+            flat = [float(a) for row in alpha_stages for a in row]
+            al = (c_double * len(flat))(*flat)
+        _check(load().lgf_batch_graph_create(c_void_p(self.h), int(nstages), f, p, g, t, al, c_void_p(cuda_stream)))
 
     def graph_launch(self, cuda_stream: int):
         _check(load().lgf_batch_graph_launch(c_void_p(self.h), c_void_p(cuda_stream)))

@@ -133,6 +133,59 @@ def test_batch_graph_replays_chained_stages(L, table8, inst):
     b.close()
 
 
+def test_batch_graph_with_per_stage_alpha(L, table8, inst):
+    # the integrating-factor argument of a HERK stage is (c~_i - c~_{i-1}) dt kappa / dx^2 (Eq.
+    # (eq:composite-LGF-IF)), so it differs between the stages of one step
+    b, meshes = make_batch(L, table8, inst)
+    fs = [torch.from_numpy(f).cuda() for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    gs = [torch.zeros_like(f) for f in fs]
+    tmps = [torch.zeros_like(f) for f in fs]
+    s = torch.cuda.Stream()
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    stage_alpha = [0.1 / 3.0, 0.2 / 3.0, 0.05]
+    table = [[a * (1.0 + 0.1 * i) for i in range(len(inst))] for a in stage_alpha]
+    b.graph_create(3, ptr(fs), ptr(phis), ptr(gs), ptr(tmps), s.cuda_stream, alpha_stages=table)
+    for t in phis + gs + tmps:
+        t.zero_()
+    torch.cuda.synchronize()
+    b.graph_launch(s.cuda_stream)
+    torch.cuda.synchronize()
+    for i, (m, f) in enumerate(zip(meshes, fs)):
+        g1, g2, phi = torch.zeros_like(f), torch.zeros_like(f), torch.zeros_like(f)
+        src = f
+        for st, dst in enumerate((g1, g2, g1)):
+            L.lgf_poisson_solve(table8, m, 3, src.data_ptr(), phi.data_ptr(), L.LGF_F64, L.make_opts(precision=2))
+            L.lgf_heat_apply(table8, m, 3, src.data_ptr(), dst.data_ptr(), L.LGF_F64, table[st][i],
+                             L.make_opts(precision=2))
+            src = dst
+        torch.cuda.synchronize()
+        assert torch.equal(g1, gs[i]), f"g instance {i}"
+        assert torch.equal(g2, tmps[i]), f"tmp instance {i}"
+        assert torch.equal(phi, phis[i]), f"phi instance {i}"
+    b.close()
+
+
+def test_batch_poisson_only_graph(L, table8, inst):
+    b, meshes = make_batch(L, table8, inst)
+    fs = [torch.from_numpy(f).cuda() for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    s = torch.cuda.Stream()
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    b.graph_create(2, ptr(fs), ptr(phis), None, None, s.cuda_stream)
+    for t in phis:
+        t.zero_()
+    torch.cuda.synchronize()
+    b.graph_launch(s.cuda_stream)
+    torch.cuda.synchronize()
+    for i, (m, f) in enumerate(zip(meshes, fs)):
+        phi = torch.zeros_like(f)
+        L.lgf_poisson_solve(table8, m, 3, f.data_ptr(), phi.data_ptr(), L.LGF_F64, L.make_opts(precision=2))
+        torch.cuda.synchronize()
+        assert torch.equal(phi, phis[i]), f"phi instance {i}"
+    b.close()
+
+
 def test_batch_rejects_mismatched_block_size(L, table8):
     m16 = L.Mesh([S.box_blocks((32, 32, 32), 16)], 16, 1.0)
     with pytest.raises(L.LgfError) as e:
