@@ -501,6 +501,46 @@ def refresh_line(L, torch, dev, steps, warmup, world, flush):
             "gpu_launches": int(rep.kernel_launches), "dtype": "df32"}
 
 
+def bump_study(L, torch, dev):
+    """The bump test of Sec. 3.4 (Fig. fig:source_correction_convergence): the manufactured streamfunction and
+    its analytic vector Laplacian on meshes with 0-3 refinement levels (alpha = 1/6, N_E = 14, 16^3 blocks),
+    solved in DF32 without the source correction, with it on Omega_k only, and with it on the extended
+    region; on the finest level the error of Psi against the analytic field and of L Psi against omega."""
+    import lgf_synth as S
+    from oracle import amr
+    table = L.lgf_table_create(16, (16, 16, 16), L.LGF_TBL_BOX_ONLY)
+    out = {}
+    for lr in range(4):
+        mesh, om, ps = S.bump_case(lr)
+        f = torch.from_numpy(np.concatenate([o[:2] for o in om], axis=1)).to(dev)
+        phi = torch.zeros_like(f)
+        k = len(mesh["levels"]) - 1
+        lv = amr.build_levels(mesh)[k]
+        B = mesh["B"]
+        wbox, pbox = np.zeros((2,) + lv.shape), np.zeros((2,) + lv.shape)
+        for i, b in enumerate(mesh["levels"][k]):
+            sl = (slice(None),) + lv.block_slice(b, B)
+            wbox[sl], pbox[sl] = om[k][:2, i], ps[k][:2, i]
+        inner = lv.omega & ~amr.dilate_maxnorm(~lv.omega, 1)
+        row = {"blocks": [len(b) for b in mesh["levels"]], "finest_h": mesh["h0"] / 2 ** k}
+        for v in (("no_correction", "correction_no_ext", "correction_ext") if lr else ("correction_ext",)):
+            m = L.Mesh(mesh["levels"], B, mesh["h0"], n_ext=0 if v == "correction_no_ext" else mesh["n_ext"])
+            flags = L.LGF_SOLVE_NO_CORRECTION if v == "no_correction" else 0
+            L.lgf_poisson_solve(table, m, 2, f.data_ptr(), phi.data_ptr(), L.LGF_F64,
+                                L.make_opts(precision=L.LGF_PREC_DF32, mac_mode=L.LGF_MAC_BOX, flags=flags))
+            torch.cuda.synchronize()
+            got = phi.cpu().numpy()[:, sum(len(b) for b in mesh["levels"][:k]):]
+            box = np.zeros((2,) + lv.shape)
+            for i, b in enumerate(mesh["levels"][k]):
+                box[(slice(None),) + lv.block_slice(b, B)] = got[:, i]
+            e_psi = float(np.abs(box - pbox)[:, lv.omega].max() / np.abs(pbox).max())
+            e_lap = float(np.abs(amr.laplacian_box(box, lv.h) - wbox)[:, inner].max() / np.abs(wbox).max())
+            row[v] = {"psi_err": e_psi, "lpsi_err": e_lap}
+        out[f"L_R={lr}"] = row
+    L.lgf_table_destroy(table)
+    return out
+
+
 def cfg2_case():
     import lgf_synth as S
     case = S.single_level_ring()
@@ -554,6 +594,7 @@ def run_gpu(args):
         extra["batch_rk3_stage"] = batch_stage_heat(L, torch, dev, max(2, args.steps // 10), 1, world)
         extra["heat_apply"] = heat_line(L, torch, dev, 10, 3, world, pk, flush)
         extra["velocity_refresh"] = refresh_line(L, torch, dev, 10, 3, world, flush)
+        extra["bump_study"] = bump_study(L, torch, dev)
     if rank == 0:
         total = hb["total"]
         mid_ms = hb["mid_ms"]

@@ -103,8 +103,14 @@ typedef struct lgf_solve_opts {
                             (relative error of a pass about 2^-(7+8(S-1)) of each cell line's largest
                             value).  BOX mode only (AUTO picks BOX where the level allows it); FP64
                             rejects S > 0 with LGF_E_UNSUPPORTED. */
-  int32_t reserved;      /* 0 */
+  int32_t flags;         /* OR of LGF_SOLVE_* (0 for the method as published) */
 } lgf_solve_opts;
+
+/* ---- lgf_solve_opts.flags
+ *  NO_CORRECTION : multi-level solves without the source correction S psi_{k-1} of Eq. (eq:source_correct):
+ *                  phi^k = P psi_{k-1} + L_k^{-1} sum_i P_{i->k} fhat_i (the uncorrected composite solve the
+ *                  bump test of Sec. 3.4 compares against; single-level solves are unaffected). */
+#define LGF_SOLVE_NO_CORRECTION 1
 
 typedef struct lgf_report {
   double ms_total;        /* with timing = 1: wall time of the call's device work */

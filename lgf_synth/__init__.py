@@ -77,6 +77,77 @@ def bump_streamfunction(nx, ny, nz, h, R=0.125, c1=1e3, c2=10.0, origin=None):
     return np.stack([f * ex, f * ey, np.zeros_like(f)])
 
 
+def _bump_fields(X, Y, Z, R, c1, c2):
+    """The bump streamfunction Psi = f(t) e_theta, t = sqrt((r - R)^2 + z^2) / R, and its vector Laplacian
+    at points (X, Y, Z), both as Cartesian components [3][...].  With f = c1 exp(-c2 / (1 - t^2)) for |t| < 1:
+    f' = f h t, f'' = f ((h t)^2 + g), h = -2 c2 / (1 - t^2)^2, g = -2 c2 (1 + 3 t^2) / (1 - t^2)^3, and in
+    cylindrical coordinates (Psi_theta = f) the vector Laplacian is
+    d^2f/dr^2 + (1/r) df/dr + d^2f/dz^2 - f / r^2 = (f'' + f h) / R^2 + f h (r - R) / (r R^2) - f / r^2."""
+    r = np.sqrt(X * X + Y * Y)
+    t2 = ((r - R) ** 2 + Z * Z) / (R * R)
+    inside = t2 < 1.0
+    q = np.where(inside, 1.0 - t2, 1.0)
+    with np.errstate(divide="ignore", over="ignore", invalid="ignore", under="ignore"):
+        f = np.where(inside, c1 * np.exp(-c2 / q), 0.0)
+        h = -2.0 * c2 / q ** 2
+        g = -2.0 * c2 * (1.0 + 3.0 * t2) / q ** 3
+        lap = (f * (h * h * t2 + g) + f * h) / R ** 2 + np.where(r > 0, f * h * (r - R) / (r * R * R) - f / r ** 2,
+                                                                 0.0)
+        lap = np.where(inside, lap, 0.0)
+        ex = np.where(r > 0, -Y / r, 0.0)
+        ey = np.where(r > 0, X / r, 0.0)
+    zero = np.zeros_like(f)
+    return np.stack([f * ex, f * ey, zero]), np.stack([lap * ex, lap * ey, zero])
+
+
+def bump_case(refinements, B=16, R=0.125, c1=1e3, c2=10.0, h0=None, alpha=1.0 / 6.0, n_ext=14):
+    """The bump test of Sec. 3.4 on a composite mesh with `refinements` levels above the base (K =
+    refinements + 1): level 0 covers the bump's support (r < 2R, |z| < R) at h0 (default R/8) dilated by
+    one block; level k+1 holds the children of level-k blocks with a cell where |omega| >
+    alpha^(refinements - k) max |omega| (the paper's criterion with L_R = refinements; taking children only
+    keeps the levels nested).  omega = the vector Laplacian of Psi, both sampled at each level's cell
+    centres.  Returns (mesh, omega_levels, psi_levels) with fields [3][nblk][B][B][B]."""
+    if h0 is None:
+        h0 = R / 8
+    K = refinements + 1
+    n0 = [int(math.ceil(4 * R / h0 / B)) * B + 2 * B] * 2 + [int(math.ceil(2 * R / h0 / B)) * B + 2 * B]
+    origin = (-n0[0] * h0 / 2, -n0[1] * h0 / 2, -n0[2] * h0 / 2)
+
+    def centres(blocks, k):
+        h = h0 / 2 ** k
+        loc = (np.arange(B) + 0.5) * h
+        out = []
+        for bx, by, bz in blocks:
+            Z, Y, X = np.meshgrid(origin[2] + bz * B * h + loc, origin[1] + by * B * h + loc,
+                                  origin[0] + bx * B * h + loc, indexing="ij")
+            out.append((X, Y, Z))
+        return out
+
+    # max |omega| from a fine sample of the support
+    xs = np.linspace(-2 * R, 2 * R, 401)
+    zs = np.linspace(-R, R, 201)
+    Zs, Xs = np.meshgrid(zs, xs, indexing="ij")
+    wmax = float(np.abs(_bump_fields(Xs, np.zeros_like(Xs), Zs, R, c1, c2)[1][1]).max())
+    levels = [box_blocks((n0[2], n0[1], n0[0]), B)]
+    kids = np.array([(i, j, l) for l in (0, 1) for j in (0, 1) for i in (0, 1)], np.int32)
+    for k in range(1, K):
+        cand = (2 * levels[k - 1][:, None, :] + kids[None]).reshape(-1, 3)
+        thr = alpha ** (refinements - (k - 1)) * wmax
+        keep = [b for b, (X, Y, Z) in zip(cand, centres(cand, k))
+                if np.abs(_bump_fields(X, Y, Z, R, c1, c2)[1]).max() > thr]
+        levels.append(np.array(sorted(map(tuple, keep)), np.int32).reshape(-1, 3))
+    om, ps = [], []
+    for k in range(K):
+        o = np.zeros((3, len(levels[k]), B, B, B))
+        p = np.zeros_like(o)
+        for i, (X, Y, Z) in enumerate(centres(levels[k], k)):
+            p[:, i], o[:, i] = _bump_fields(X, Y, Z, R, c1, c2)
+        om.append(o)
+        ps.append(p)
+    mesh = dict(B=B, h0=h0, n_ext=n_ext, levels=[np.ascontiguousarray(b, dtype=np.int32) for b in levels])
+    return mesh, om, ps
+
+
 def box_blocks(shape, B: int) -> np.ndarray:
     """Block coordinates (bx, by, bz) tiling a [nz][ny][nx] box whose sides are multiples of B."""
     nz, ny, nx = shape

@@ -220,11 +220,13 @@ def _to_blocks(lv, blocks, box, B):
     return out
 
 
-def flgf_amr(mesh, f_levels, return_internals=False):
+def flgf_amr(mesh, f_levels, return_internals=False, correction=True):
     """FLGF-AMR solve (Sec. 3.4).  ``f_levels[k]`` is [ncomp][nblk_k][B]^3 user data of level k.
 
     Returns per level [ncomp][nblk_k][B]^3 arrays holding phi^k on Omega_k and 0 elsewhere, and the
-    Omega_k masks in the same block layout.
+    Omega_k masks in the same block layout.  ``correction=False`` drops the source correction
+    (``s_k = 0``): the uncorrected composite solve ``phi^k = P psi_{k-1} + L_k^{-1} sum_i P_{i->k} fhat_i``
+    that the bump test of Sec. 3.4 (Fig. fig:source_correction_convergence) compares against.
     """
     B, n_ext = mesh["B"], mesh.get("n_ext", 16)
     blocks = mesh["levels"]
@@ -247,7 +249,7 @@ def flgf_amr(mesh, f_levels, return_internals=False):
         ext = dilate_maxnorm(lv[k].omega, n_ext) & ~lv[k].omega
         region = lv[k].omega | ext
         assert np.all(np.isfinite(s[:, region])), "level box too small for the correction region"
-        s = np.where(region[None], s, 0.0)
+        s = np.where(region[None], s, 0.0) if correction else np.zeros_like(c)
         A = s + fhat[k]
         phi[k] = c + solve_level_box(A + (F[k] - fhat[k]), lv[k])
         psi[k] = c + solve_level_box(A, lv[k])

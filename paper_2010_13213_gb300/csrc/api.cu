@@ -234,6 +234,7 @@ int lgf_poisson_solve(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void
   if (o.precision < 0 || o.precision > 2) return set_error(LGF_E_INVALID_ARG, "precision %d", o.precision);
   if (o.mac_mode < 0 || o.mac_mode > 2) return set_error(LGF_E_INVALID_ARG, "mac_mode %d", o.mac_mode);
   if ((rc = check_slices(o))) return rc;
+  if (o.flags & ~LGF_SOLVE_NO_CORRECTION) return set_error(LGF_E_INVALID_ARG, "unknown solve flags 0x%x", o.flags);
   if (rep) memset(rep, 0, sizeof(*rep));
   return solve_poisson(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream);
 }
@@ -260,6 +261,7 @@ int lgf_refinement_indicator(lgf_table *t, const lgf_mesh *m, int32_t ncomp, con
   if (o.precision < 0 || o.precision > 2) return set_error(LGF_E_INVALID_ARG, "precision %d", o.precision);
   if (o.mac_mode < 0 || o.mac_mode > 2) return set_error(LGF_E_INVALID_ARG, "mac_mode %d", o.mac_mode);
   if ((rc = check_slices(o))) return rc;
+  if (o.flags & ~LGF_SOLVE_NO_CORRECTION) return set_error(LGF_E_INVALID_ARG, "unknown solve flags 0x%x", o.flags);
   if (rep) memset(rep, 0, sizeof(*rep));
   return solve_multi(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream, ind);
 }

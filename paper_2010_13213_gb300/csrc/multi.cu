@@ -239,14 +239,15 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
       LGF_LAUNCH_CHECK("interp");
       tm.mark(PH_INTERP);
     }
+    const bool corr = k > 0 && !(o.flags & LGF_SOLVE_NO_CORRECTION);
     if (nSA) {
-      if (k > 0) {  // L_{k-1} psi_{k-1} once per coarse cell, then interpolated per fine cell
+      if (corr) {  // L_{k-1} psi_{k-1} once per coarse cell, then interpolated per fine cell
         k_lap<R><<<dim3((unsigned)P->L[k - 1].BL.size(), ncomp), 256, 0, st>>>(Lc, P->L[k - 1].d_BL, psi_prev, Lpsi,
                                                                                ccs);
         LGF_LAUNCH_CHECK("coarse Laplacian");
       }
       k_correct<R><<<dim3(nSA, ncomp), 256, 0, st>>>(Ld, L.d_BL, lists + L.off_SA, f, dtype, ucs, A, cs[k], c, Lc,
-                                                     Lpsi, ccs, k > 0);
+                                                     Lpsi, ccs, corr);
       LGF_LAUNCH_CHECK("correct");
       tm.mark(PH_CORRECT);
     }

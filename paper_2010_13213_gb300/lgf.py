@@ -29,6 +29,7 @@ LGF_F64, LGF_F32 = 0, 1
 LGF_PREC_FP64, LGF_PREC_FP32, LGF_PREC_DF32 = 0, 1, 2
 LGF_MAC_AUTO, LGF_MAC_PAIR, LGF_MAC_BOX = 0, 1, 2
 LGF_TBL_FP64, LGF_TBL_FP32, LGF_TBL_DF32, LGF_TBL_BOX_ONLY = 1, 2, 4, 8
+LGF_SOLVE_NO_CORRECTION = 1
 PHASES = ("restrict", "correction", "forward", "mac", "inverse", "interp", "residual", "heat")
 
 
@@ -46,7 +47,7 @@ class lgf_mesh(ctypes.Structure):
 
 class lgf_solve_opts(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("mac_mode", c_int32), ("residual", c_int32),
-                ("timing", c_int32), ("residual_tol", c_double), ("dft_slices", c_int32), ("reserved", c_int32)]
+                ("timing", c_int32), ("residual_tol", c_double), ("dft_slices", c_int32), ("flags", c_int32)]
 
 
 class lgf_report(ctypes.Structure):
@@ -164,9 +165,10 @@ def lgf_table_lgf_values(table, n: int) -> np.ndarray:
     return out.reshape(n + 1, n + 1, n + 1)
 
 
-def _opts(precision=LGF_PREC_FP64, mac_mode=LGF_MAC_AUTO, residual=0, timing=0, residual_tol=0.0, dft_slices=0):
+def _opts(precision=LGF_PREC_FP64, mac_mode=LGF_MAC_AUTO, residual=0, timing=0, residual_tol=0.0, dft_slices=0,
+          flags=0):
     return lgf_solve_opts(int(precision), int(mac_mode), int(residual), int(timing), float(residual_tol),
-                          int(dft_slices), 0)
+                          int(dft_slices), int(flags))
 
 
 def lgf_device_status(table) -> None:

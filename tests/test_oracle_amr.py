@@ -207,3 +207,24 @@ def test_heat_second_moment_gives_the_same_physical_increment_on_every_level(whi
         assert deep.sum() > 200, k
         inc = (g[k] - q[k])[0][deep]
         assert np.abs(inc - expected).max() < 1e-10 * expected, (k, inc.min(), inc.max(), expected)
+
+
+def test_uncorrected_solve_satisfies_its_own_identity():
+    # without the source correction phi^k = c_k + L_k^{-1} F_k, so L_k (phi^k - c_k) = F_k on the level box
+    # interior, while the corrected identity L_k phi^k = F_k + P L_{k-1} psi_{k-1} fails by the correction
+    mesh = _two_level_mesh(n_ext=4)
+    f = _gaussian_levels(mesh)
+    out, masks, I = amr.flgf_amr(mesh, f, return_internals=True, correction=False)
+    lv, phi, psi, F = I["levels"], I["phi"], I["psi"], I["F"]
+    c = I["steps"][0]["c"]
+    assert np.abs(I["steps"][0]["s"]).max() == 0.0
+    inner = lv[1].omega & ~amr.dilate_maxnorm(~lv[1].omega, 1)
+    lhs = amr.laplacian_box(phi[1] - c, lv[1].h)
+    d = np.abs(lhs - F[1])[:, inner]
+    assert np.isfinite(d).all() and d.max() < 1e-10 * np.abs(F[1][:, inner]).max()
+    corrected = F[1] + amr.interp_up(amr.laplacian_box(psi[0], lv[0].h), lv[0], lv[1])
+    miss = np.abs(amr.laplacian_box(phi[1], lv[1].h) - corrected)[:, inner].max()
+    assert miss > 1e-6 * np.abs(corrected[:, inner]).max()
+    # and it differs from the corrected solve by more than rounding
+    ref, _ = amr.flgf_amr(mesh, f)
+    assert np.abs(out[1] - ref[1])[:, masks[1]].max() > 1e-6 * np.abs(ref[1][:, masks[1]]).max()
