@@ -216,9 +216,12 @@ __global__ void __launch_bounds__(256) k_residual(LevelDev L, const int4 *blocks
                phi_at(x, y - 1, z, ok) + phi_at(x, y, z + 1, ok) + phi_at(x, y, z - 1, ok);
     if (!ok) continue;
     double src = RT<R>::to_d(F[comp * cs + (int64_t)b * B3 + off]);
-    if (has_coarse) {
+    if (has_coarse) {  // P L_{k-1} psi_{k-1} in FP64 arithmetic on the stored psi values
       src += interp_at<double>(x, y, z, [&](int i, int j, int k) {
-        return RT<R>::to_d(lap7<R>(Lc, psi, pcs, comp, i, j, k, RT<R>::from(inv_h2c)));
+        auto pv = [&](int a, int bb, int c) { return RT<R>::to_d(fetch<R>(Lc, psi, pcs, comp, a, bb, c)); };
+        const double nb = pv(i + 1, j, k) + pv(i - 1, j, k) + pv(i, j + 1, k) + pv(i, j - 1, k) + pv(i, j, k + 1) +
+                          pv(i, j, k - 1);
+        return (nb - 6.0 * pv(i, j, k)) * inv_h2c;
       });
     }
     const double ar = fabs((s - 6.0 * c0) * inv_h2f - src);

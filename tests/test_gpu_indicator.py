@@ -57,7 +57,7 @@ def _split(arr, mesh):
 
 
 def _check(got, ref, mesh, tol, ratio_margin):
-    rms, flags, smax = got
+    rms, flags, smax = got[:3]
     scale = max(r.max() for r in ref["rms"])
     for k, (r, g) in enumerate(zip(ref["rms"], _split(rms, mesh))):
         assert np.abs(g - r).max() <= tol * scale, k
