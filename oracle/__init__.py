@@ -13,11 +13,13 @@ Contents
            FIF-AMR heat apply (Sec. 3.5, Eq. (eq:FIF-AMR)) on dense per-level boxes.
 ``refresh`` the velocity refresh u = -C^T L_E^{-1} omega (Sec. 4.1, Eq. (eq:vel_update)).
 ``refine`` the refinement indicator from the combined source (Sec. 4.2, Eqs. (eq:refine1)-(eq:refine2)).
+``projection`` the HERK stage projection L p = D r, u = H (r - G p) (Sec. 2.4, Sec. 3.6).
 
 Parity status (which functions are pinned by something other than themselves) is listed in the
 module docstrings; every function here is pinned except where a docstring says "parity unpinned".
 """
 from .core import *  # noqa: F401,F403
 from . import amr  # noqa: F401
+from . import projection  # noqa: F401
 from . import refine  # noqa: F401
 from . import refresh  # noqa: F401
