@@ -220,6 +220,31 @@ int lgf_velocity_refresh(lgf_table *t, const lgf_mesh *m, const void *omega_dev,
                          const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream);
 
 /*
+ * lgf_stage_projection -- the pressure projection of one half-explicit Runge-Kutta stage on the AMR grid
+ * (Sec. 2.4, Eqs. (eq:projection-1), (eq:projection-2); Sec. 3.6, Eqs. (eq:approx0)-(eq:approx4)):
+ *     L_C p = D r,    u = H (r - G p),     H = the integrating factor E_alpha of lgf_heat_apply.
+ * Staggered lattice (Sec. 2.1): component a of a face field (r, u) at cell n is stored at index n and sits on
+ * the face n + (1/2, 1/2, 1/2) + e_a / 2; p sits at the cell centre.  D r(n) = sum_a (r_a[n] - r_a[n - e_a]) / h,
+ * (G p)_a[n] = (p[n + e_a] - p[n]) / h, so D G = L_C (Eq. (eq:mimetic)).  On the AMR grid:
+ *     D^r   = D (P_k r^) on Omega_k, P_k r^ the level-k reconstruction (own values on Omega_k, interpolation
+ *             of coarser and 8-child means of finer levels, each component as a cell-centred scalar), which
+ *             supplies the faces across the Omega_k boundary (the one-cell-larger restriction of Sec. 3.6);
+ *     p^    = FLGF-AMR(D^r) on Omega_k (lgf_poisson_solve);
+ *     w^    = r^ - G (P_k p^) on Omega_k;
+ *     u^    = FIF-AMR(w^) (lgf_heat_apply with alpha_finest).
+ * Fields outside the AMR grid are zero (the computational domain's truncation, Sec. 4.1).
+ *   r_dev        : device [3][sum nblocks][B^3] in dtype, read on Omega_k.
+ *   u_dev        : device [3][sum nblocks][B^3] in dtype, written on Omega_k.
+ *   p_dev        : device [1][sum nblocks][B^3] in dtype or NULL; receives p^ on Omega_k when given.
+ *   alpha_finest : kappa (c~_i - c~_{i-1}) dt / dx_finest^2 of the stage (Eq. (eq:composite-LGF-IF)).
+ *   opts         : precision / mac_mode / flags of the Poisson solve and the arithmetic of the IF; may be NULL.
+ * block_role is ignored (every block carries r and receives u).  Scratch (D^r, p^, w^) is held by the table
+ * per stream.  Errors: as lgf_poisson_solve and lgf_heat_apply.
+ */
+int lgf_stage_projection(lgf_table *t, const lgf_mesh *m, const void *r_dev, void *u_dev, void *p_dev, int32_t dtype,
+                         double alpha_finest, const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream);
+
+/*
  * lgf_refinement_indicator -- the Poisson solve of lgf_poisson_solve together with the refinement
  * indicator of the adaptive mesh (Sec. 4.2, Eqs. (eq:refine1), (eq:maximumS), (eq:refine2)), reduced on
  * the device from the combined source the solve builds anyway (Eq. (eq:combined_source)):

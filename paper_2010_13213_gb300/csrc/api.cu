@@ -266,6 +266,27 @@ int lgf_refinement_indicator(lgf_table *t, const lgf_mesh *m, int32_t ncomp, con
   return solve_multi(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream, ind);
 }
 
+int lgf_stage_projection(lgf_table *t, const lgf_mesh *m, const void *r_dev, void *u_dev, void *p_dev, int32_t dtype,
+                         double alpha_finest, const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream) {
+  if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");
+  int rc = check_mesh(m, t->B);
+  if (rc) return rc;
+  if (!r_dev || !u_dev) return set_error(LGF_E_INVALID_ARG, "field pointer NULL");
+  if (r_dev == u_dev || (p_dev && (p_dev == r_dev || p_dev == u_dev)))
+    return set_error(LGF_E_INVALID_ARG, "r, u and p must not alias");
+  if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
+  if (!(alpha_finest >= 0.0) || alpha_finest > 1e4)
+    return set_error(LGF_E_INVALID_ARG, "alpha_finest %g", alpha_finest);
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0, 0, 0};
+  if (opts) o = *opts;
+  if (o.precision < 0 || o.precision > 2) return set_error(LGF_E_INVALID_ARG, "precision %d", o.precision);
+  if (o.mac_mode < 0 || o.mac_mode > 2) return set_error(LGF_E_INVALID_ARG, "mac_mode %d", o.mac_mode);
+  if ((rc = check_slices(o))) return rc;
+  if (o.flags & ~LGF_SOLVE_NO_CORRECTION) return set_error(LGF_E_INVALID_ARG, "unknown solve flags 0x%x", o.flags);
+  if (rep) memset(rep, 0, sizeof(*rep));
+  return solve_projection(t, m, r_dev, u_dev, p_dev, dtype, alpha_finest, o, rep, (cudaStream_t)cuda_stream);
+}
+
 int lgf_heat_apply(lgf_table *t, const lgf_mesh *m, int32_t ncomp, const void *f_dev, void *g_dev,
                    int32_t dtype, double alpha_finest, const lgf_solve_opts *opts, lgf_report *rep,
                    void *cuda_stream) {

@@ -624,6 +624,203 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
   return LGF_OK;
 }
 
+// ------------------------------------------------------------------ HERK stage projection (Sec. 2.4, Sec. 3.6)
+// Staggered fields: component a of a face field at cell n sits on the face n + (1/2,1/2,1/2) + e_a/2; the
+// pressure at the cell centre.  D r(n) = sum_a (r_a[n] - r_a[n - e_a]) / h, (G p)_a[n] = (p[n + e_a] - p[n]) / h.
+
+// D^r on the Omega_k cells of the caller's level-k blocks from the reconstruction T = P_k r^ (3 components,
+// internal layout); 0 on the other cells.  grid (nU_k), 256 threads; out in the caller's layout (dtype).
+template <class R>
+__global__ void __launch_bounds__(256) k_proj_div(LevelDev L, const int4 *blocks, const R *T, int64_t cs, void *out,
+                                                  int dtype, int64_t user_off) {
+  const int b = blockIdx.x, sh = L.shift, B = 1 << sh, B3 = B * B * B;
+  const int4 bc = blocks[b];
+  const double inv_h = 1.0 / L.h;
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    double d = 0.0;
+    if (L.cellmask[(int64_t)b * B3 + off] & 1) {
+      const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+                z = (bc.z << sh) + (off >> (2 * sh));
+      const double here = RT<R>::to_d(T[(int64_t)b * B3 + off]) + RT<R>::to_d(T[cs + (int64_t)b * B3 + off]) +
+                          RT<R>::to_d(T[2 * cs + (int64_t)b * B3 + off]);
+      const double back = RT<R>::to_d(fetch<R>(L, T, cs, 0, x - 1, y, z)) +
+                          RT<R>::to_d(fetch<R>(L, T, cs, 1, x, y - 1, z)) +
+                          RT<R>::to_d(fetch<R>(L, T, cs, 2, x, y, z - 1));
+      d = (here - back) * inv_h;
+    }
+    store_field(out, (user_off + b) * (int64_t)B3 + off, dtype, d);
+  }
+}
+
+// w^ = r^ - G p on the Omega_k cells from the caller's r and the reconstruction T = P_k p^ (1 component); 0 on
+// the other cells.  grid (nU_k, 3).
+template <class R>
+__global__ void __launch_bounds__(256) k_proj_grad(LevelDev L, const int4 *blocks, const R *T, int64_t cs,
+                                                   const void *r, void *w, int dtype, int64_t ucs, int64_t user_off) {
+  const int b = blockIdx.x, a = blockIdx.y, sh = L.shift, B = 1 << sh, B3 = B * B * B;
+  const int4 bc = blocks[b];
+  const double inv_h = 1.0 / L.h;
+  const int64_t o0 = a * ucs + (user_off + b) * (int64_t)B3;
+  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
+    double v = 0.0;
+    if (L.cellmask[(int64_t)b * B3 + off] & 1) {
+      const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
+                z = (bc.z << sh) + (off >> (2 * sh));
+      const double pn = RT<R>::to_d(T[(int64_t)b * B3 + off]);
+      const double pe = RT<R>::to_d(fetch<R>(L, T, cs, 0, x + (a == 0), y + (a == 1), z + (a == 2)));
+      v = load_field<double>(r, o0 + off, dtype) - (pe - pn) * inv_h;
+    }
+    store_field(w, o0 + off, dtype, v);
+  }
+}
+
+// P_k f^ of every level on the plan's heat block set (own values on Omega_k, interpolation of the coarser
+// levels, 8-child means of the finer ones; as in FIF-AMR); consume(k, T, cs_k) runs after level k's T.
+template <class R, class Consume>
+static int reconstruct_levels(Plan *P, const lgf_mesh *m, int ncomp, const void *f, int dtype, Workspace *ws,
+                              int64_t &launches, cudaStream_t st, Consume consume) {
+  const int K = P->K, B = P->B;
+  const int64_t B3 = (int64_t)B * B * B;
+  int64_t total_user = 0, maxBL = 0;
+  for (int k = 0; k < K; ++k) total_user += P->L[k].nU, maxBL = std::max<int64_t>(maxBL, P->L[k].BL.size());
+  const int64_t ucs = total_user * B3;
+  std::vector<int64_t> Foff(K + 1, 0), cs(K);
+  for (int k = 0; k < K; ++k) {
+    cs[k] = (int64_t)P->L[k].BL.size() * B3;
+    Foff[k + 1] = Foff[k] + ncomp * cs[k];
+  }
+  const size_t field = sizeof(R) * (size_t)ncomp * maxBL * B3;
+  int rc;
+  if ((rc = ws->buf[10].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[11].reserve(field)) ||
+      (rc = ws->buf[13].reserve(field)) || (rc = ws->buf[14].reserve(field)))
+    return rc;
+  R *Fall = (R *)ws->buf[10].p, *T = (R *)ws->buf[11].p, *Uprev = (R *)ws->buf[13].p, *Ucur = (R *)ws->buf[14].p;
+  for (int k = K - 1; k >= 0; --k) {
+    const LevelPlan &L = P->L[k];
+    const LevelDev Ld = level_dev(P, k, m->h0);
+    k_restrict<R><<<dim3(L.nU, ncomp), 256, 0, st>>>(Ld, f, dtype, ucs, L.user_off, Fall + Foff[k], cs[k]);
+    LGF_LAUNCH_CHECK("restrict");
+    if (k + 1 < K) {
+      const LevelPlan &Lf = P->L[k + 1];
+      k_coarsen_add<R><<<dim3(Lf.nU, ncomp), 256, 0, st>>>(Ld, Fall + Foff[k], cs[k], Lf.d_BL, Fall + Foff[k + 1],
+                                                          cs[k + 1]);
+      LGF_LAUNCH_CHECK("coarsen");
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    const LevelPlan &L = P->L[k];
+    const LevelDev Ld = level_dev(P, k, m->h0);
+    const LevelDev Lc = k > 0 ? level_dev(P, k - 1, m->h0) : Ld;
+    const int nHB = (int)L.HB.size();
+    const int32_t *HB = L.d_lists + L.off_HB;
+    const size_t bytes = sizeof(R) * (size_t)ncomp * L.BL.size() * B3;
+    cudaMemsetAsync(T, 0, bytes, st);
+    if (k + 1 < K) {
+      cudaMemsetAsync(Ucur, 0, bytes, st);
+      k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 0, f, dtype, ucs, Fall + Foff[k], L.nU, Ucur,
+                                                        cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
+      LGF_LAUNCH_CHECK("reconstruction U");
+    }
+    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 1, f, dtype, ucs, Fall + Foff[k], L.nU, T,
+                                                      cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
+    LGF_LAUNCH_CHECK("reconstruction");
+    if ((rc = consume(k, Ld, (const R *)T, cs[k]))) return rc;
+    ++launches;
+    std::swap(Uprev, Ucur);
+  }
+  return LGF_OK;
+}
+
+template <class R>
+static int projection_t(lgf_table *t, const lgf_mesh *m_in, const void *r, void *u, void *p_out, int dtype,
+                        double alpha, const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  lgf_mesh m = *m_in;
+  m.block_role = nullptr;  // every block carries r and receives u
+  const int K = m.nlevels;
+  std::vector<int> radii(K, 1);  // the reconstructions are read one cell around Omega_k
+  Plan *P = nullptr;
+  int rc = get_plan(&m, radii.data(), &P);
+  if (rc) return rc;
+  const int B = P->B;
+  const int64_t B3 = (int64_t)B * B * B;
+  int64_t total_user = 0;
+  for (int k = 0; k < K; ++k) total_user += P->L[k].nU;
+  const int64_t ucs = total_user * B3;
+  const size_t es = dtype == LGF_F32 ? 4 : 8;
+  Workspace *ws = workspace_for(t, st);
+  if ((rc = ws->buf[18].reserve(es * (size_t)ucs)) || (rc = ws->buf[19].reserve(es * (size_t)ucs)) ||
+      (rc = ws->buf[20].reserve(3 * es * (size_t)ucs)))
+    return rc;
+  void *d = ws->buf[18].p, *w = ws->buf[20].p;
+  void *p = p_out ? p_out : ws->buf[19].p;
+  int64_t launches = 0;
+  PhaseTimer tm;
+  tm.start(o.timing != 0, st);
+  // 1. D^r on Omega_k from P_k r^
+  rc = reconstruct_levels<R>(P, &m, 3, r, dtype, ws, launches, st,
+                             [&](int k, const LevelDev &Ld, const R *T, int64_t cs) {
+                               const LevelPlan &L = P->L[k];
+                               k_proj_div<R><<<L.nU, 256, 0, st>>>(Ld, L.d_BL, T, cs, d, dtype, L.user_off);
+                               cudaError_t e = cudaGetLastError();
+                               return e == cudaSuccess ? LGF_OK
+                                                       : set_error(LGF_E_CUDA, "divergence launch: %s",
+                                                                   cudaGetErrorString(e));
+                             });
+  if (rc) return rc;
+  tm.mark(PH_CORRECT);
+  // 2. L_C p = D^r (FLGF-AMR)
+  lgf_solve_opts so = o;
+  so.timing = 0;
+  so.residual = 0;
+  lgf_report srep{};
+  if ((rc = solve_poisson(t, &m, 1, d, p, dtype, so, &srep, st))) return rc;
+  launches += srep.kernel_launches;
+  tm.mark(PH_MAC);
+  // 3. w^ = r^ - G P_k p^ on Omega_k
+  rc = reconstruct_levels<R>(P, &m, 1, p, dtype, ws, launches, st,
+                             [&](int k, const LevelDev &Ld, const R *T, int64_t cs) {
+                               const LevelPlan &L = P->L[k];
+                               k_proj_grad<R><<<dim3(L.nU, 3), 256, 0, st>>>(Ld, L.d_BL, T, cs, r, w, dtype, ucs,
+                                                                            L.user_off);
+                               cudaError_t e = cudaGetLastError();
+                               return e == cudaSuccess ? LGF_OK
+                                                       : set_error(LGF_E_CUDA, "gradient launch: %s",
+                                                                   cudaGetErrorString(e));
+                             });
+  if (rc) return rc;
+  tm.mark(PH_INTERP);
+  // 4. u^ = FIF-AMR(w^)
+  lgf_report hrep{};
+  if ((rc = solve_heat(t, &m, 3, w, u, dtype, alpha, so, &hrep, st))) return rc;
+  launches += hrep.kernel_launches;
+  tm.mark(PH_HEAT);
+  tm.finish(rep);
+  if (rep) {
+    rep->target_cells = hrep.target_cells;
+    rep->kernel_launches = launches;
+    rep->source_blocks = srep.source_blocks;
+    rep->target_blocks = srep.target_blocks;
+    rep->mac_mode_used = srep.mac_mode_used;
+    rep->scratch_bytes = (int64_t)ws->total() + (int64_t)P->device_bytes;
+    rep->alg_bytes = srep.alg_bytes;
+    rep->alg_flops = srep.alg_flops;
+  }
+  if (o.timing) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(LGF_E_CUDA, "projection failed: %s", cudaGetErrorString(e));
+  }
+  return LGF_OK;
+}
+
+int solve_projection(lgf_table *t, const lgf_mesh *m, const void *r, void *u, void *p, int dtype, double alpha,
+                     const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
+  switch (o.precision) {
+    case LGF_PREC_FP64: return projection_t<double>(t, m, r, u, p, dtype, alpha, o, rep, st);
+    case LGF_PREC_FP32: return projection_t<float>(t, m, r, u, p, dtype, alpha, o, rep, st);
+    default: return projection_t<df>(t, m, r, u, p, dtype, alpha, o, rep, st);
+  }
+}
+
 int solve_heat(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype, double alpha,
                const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st) {
   if (o.precision == LGF_PREC_FP32) return heat_t<float>(t, m, ncomp, f, g, dtype, alpha, o, rep, st);

@@ -10,6 +10,8 @@ int solve_poisson(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
                   const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st);
 int solve_multi(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *phi, int dtype,
                 const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st, const lgf_indicator *ind);
+int solve_projection(lgf_table *t, const lgf_mesh *m, const void *r, void *u, void *p, int dtype, double alpha,
+                     const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st);
 int solve_heat(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, void *g, int dtype,
                double alpha_finest, const lgf_solve_opts &o, lgf_report *rep, cudaStream_t st);
 

@@ -89,6 +89,8 @@ def load():
                                                  c_int32, c_int32, c_void_p]
         lib.lgf_velocity_refresh.argtypes = [c_void_p, POINTER(lgf_mesh), c_void_p, c_void_p, c_int32,
                                              POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
+        lib.lgf_stage_projection.argtypes = [c_void_p, POINTER(lgf_mesh), c_void_p, c_void_p, c_void_p, c_int32,
+                                             c_double, POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
         lib.lgf_refinement_indicator.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p, c_int32,
                                                  POINTER(lgf_solve_opts), POINTER(lgf_indicator),
                                                  POINTER(lgf_report), c_void_p]
@@ -106,7 +108,7 @@ def load():
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
                      "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_velocity_refresh",
-                     "lgf_refinement_indicator", "lgf_batch_create",
+                     "lgf_refinement_indicator", "lgf_stage_projection", "lgf_batch_create",
                      "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
                      "lgf_device_status", "lgf_selftest_wait_timeout"):
@@ -202,6 +204,17 @@ def lgf_refinement_indicator(table, mesh: Mesh, ncomp: int, f_dev: int, phi_dev:
                                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(ind),
                                            ctypes.byref(report) if report is not None else None,
                                            c_void_p(cuda_stream or None)))
+
+
+def lgf_stage_projection(table, mesh: Mesh, r_dev: int, u_dev: int, p_dev: int, dtype: int, alpha_finest: float,
+                         opts: lgf_solve_opts | None = None, report: lgf_report | None = None,
+                         cuda_stream: int = 0) -> None:
+    """L_C p = D r, u = H(r - G p) on the AMR grid; p_dev may be 0 (pressure not returned)."""
+    _check(load().lgf_stage_projection(c_void_p(table), ctypes.byref(mesh.c), c_void_p(r_dev), c_void_p(u_dev),
+                                       c_void_p(p_dev or None), int(dtype), float(alpha_finest),
+                                       ctypes.byref(opts) if opts is not None else None,
+                                       ctypes.byref(report) if report is not None else None,
+                                       c_void_p(cuda_stream or None)))
 
 
 def lgf_heat_apply(table, mesh: Mesh, ncomp: int, f_dev: int, g_dev: int, dtype: int, alpha_finest: float,
