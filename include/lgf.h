@@ -333,6 +333,22 @@ int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_d
                            void *const *g_dev, void *const *tmp_dev, const double *alpha_stages,
                            void *cuda_stream);
 int lgf_batch_graph_launch(lgf_batch *b, void *cuda_stream);
+
+/*
+ * lgf_batch_autotune -- measure and choose how the batch runs (the batched solver's autotuner):
+ *   (i)  per instance, the evaluation of its block-index DFT passes: the CUDA-core conjugate-pair passes or,
+ *        for DF32 / FP32 solves, the tensor-core DFT-GEMM with 5 / 3 digit slices (the fewest that keep the
+ *        arithmetic's accuracy), whichever solves the instance faster (three timed solves each);
+ *   (ii) the instance order, longest measured solve first, dealt to the least-loaded stream;
+ *   (iii) the stream count from {4, 8, 16, 32}, by timing whole eager Poisson stages.
+ * f_dev / phi_dev: the instances' fields (phi is overwritten).  Synchronises cuda_stream.  A graph captured
+ * before the call keeps the old choices; capture after it.
+ */
+int lgf_batch_autotune(lgf_batch *b, const void *const *f_dev, void *const *phi_dev, void *cuda_stream);
+
+/* lgf_batch_tuning -- the choices: stream count, per-instance digit slices (0 = CUDA-core passes) and measured
+ * solve time in ms (0 before lgf_batch_autotune).  Each output pointer may be NULL; slices and ms hold ninst. */
+int lgf_batch_tuning(const lgf_batch *b, int32_t *nstreams, int32_t *slices, double *ms);
 int lgf_batch_graph_nodes(const lgf_batch *b, int64_t *nodes);
 
 /*

@@ -26,6 +26,9 @@ struct lgf_batch {
   std::vector<std::vector<int32_t>> nbk, ijk;      // per instance owned copies
   std::vector<double> alpha;
   std::vector<double> cost;
+  std::vector<lgf_solve_opts> opts_i;             // per instance (the autotuner's DFT-pass choice)
+  std::vector<double> tuned_ms;                   // per instance: measured solve time (ms), 0 before tuning
+  bool tuned = false;
   std::vector<std::vector<int>> by_stream;         // instance lists per stream
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> ev_join;
@@ -49,7 +52,7 @@ static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, voi
     cudaStream_t ss = b->streams[s];
     cudaStreamWaitEvent(ss, b->ev_fork, 0);
     for (int i : b->by_stream[s]) {
-      int rc = lgf_poisson_solve(b->t, &b->mesh[i], b->ncomp, f[i], phi[i], b->dtype, &b->opts, nullptr, ss);
+      int rc = lgf_poisson_solve(b->t, &b->mesh[i], b->ncomp, f[i], phi[i], b->dtype, &b->opts_i[i], nullptr, ss);
       if (rc) return rc;
       if (g && g[i]) {
         rc = lgf_heat_apply(b->t, &b->mesh[i], b->ncomp, f[i], g[i], b->dtype, alpha ? alpha[i] : b->alpha[i],
@@ -62,6 +65,34 @@ static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, voi
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "batch stage: %s", cudaGetErrorString(e));
+}
+
+// Longest-processing-time-first assignment of the instances to `nstreams` streams (created on demand),
+// by the measured solve times once the batch is tuned, else by block counts.
+static int schedule(lgf_batch *b, int nstreams) {
+  nstreams = std::max(1, std::min(nstreams, b->n));
+  const std::vector<double> &w = b->tuned ? b->tuned_ms : b->cost;
+  std::vector<int> order(b->n);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return w[a] > w[c]; });
+  b->by_stream.assign(nstreams, {});
+  std::vector<double> load(nstreams, 0.0);
+  for (int i : order) {
+    const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->by_stream[s].push_back(i);
+    load[s] += w[i];
+  }
+  while ((int)b->streams.size() < nstreams) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return set_error(LGF_E_CUDA, "batch stream creation failed");
+    b->streams.push_back(s);
+    b->ev_join.push_back(e);
+  }
+  b->nstreams = nstreams;
+  return LGF_OK;
 }
 
 extern "C" {
@@ -103,25 +134,12 @@ int lgf_batch_create(lgf_batch **out, lgf_table *t, int32_t ninst, const lgf_mes
     b->alpha[i] = alpha ? alpha[i] : 0.0;
     b->cost[i] = (double)tot;
   }
-  // longest-processing-time-first assignment of instances to streams
-  std::vector<int> order(ninst);
-  std::iota(order.begin(), order.end(), 0);
-  std::sort(order.begin(), order.end(), [&](int a, int c) { return b->cost[a] > b->cost[c]; });
-  b->by_stream.assign(b->nstreams, {});
-  std::vector<double> load(b->nstreams, 0.0);
-  for (int i : order) {
-    const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    b->by_stream[s].push_back(i);
-    load[s] += b->cost[i];
-  }
-  b->streams.resize(b->nstreams);
-  b->ev_join.resize(b->nstreams);
-  for (int s = 0; s < b->nstreams; ++s) {
-    if (cudaStreamCreateWithFlags(&b->streams[s], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_join[s], cudaEventDisableTiming) != cudaSuccess) {
-      delete b;
-      return set_error(LGF_E_CUDA, "batch stream creation failed");
-    }
+  b->opts_i.assign(ninst, b->opts);
+  b->tuned_ms.assign(ninst, 0.0);
+  int rc = schedule(b, b->nstreams);
+  if (rc) {
+    delete b;
+    return rc;
   }
   if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
     delete b;
@@ -198,6 +216,75 @@ int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_d
   }
   b->graph = graph;
   b->graph_stages = nstages;
+  return LGF_OK;
+}
+
+int lgf_batch_autotune(lgf_batch *b, const void *const *f_dev, void *const *phi_dev, void *cuda_stream) {
+  if (!b || !f_dev || !phi_dev) return set_error(LGF_E_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // candidate evaluations of the block-index DFT passes: the CUDA-core passes, and for the FP32-hardware
+  // arithmetics the tensor-core DFT-GEMM with the fewest slices that keeps the arithmetic's accuracy
+  std::vector<int> cand = {0};
+  if (b->opts.dft_slices == 0 && b->opts.mac_mode != LGF_MAC_PAIR) {
+    if (b->opts.precision == LGF_PREC_DF32) cand.push_back(5);
+    if (b->opts.precision == LGF_PREC_FP32) cand.push_back(3);
+  }
+  for (int i = 0; i < b->n; ++i) {
+    double best = 1e300;
+    int best_s = b->opts_i[i].dft_slices;
+    for (int sl : cand) {
+      lgf_solve_opts o = b->opts;
+      o.dft_slices = sl;
+      o.timing = 1;
+      double t = 1e300;
+      for (int rep = 0; rep < 3; ++rep) {  // the first call builds plans and spectra
+        lgf_report r{};
+        int rc = lgf_poisson_solve(b->t, &b->mesh[i], b->ncomp, f_dev[i], phi_dev[i], b->dtype, &o, &r, st);
+        if (rc) return rc;
+        if (rep) t = std::min(t, r.ms_total);
+      }
+      if (t < best) best = t, best_s = sl;
+    }
+    b->opts_i[i].dft_slices = best_s;
+    b->tuned_ms[i] = best;
+  }
+  b->tuned = true;
+  // the stream count: whole eager stages timed on the caller's stream
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_error(LGF_E_CUDA, "event creation failed");
+  double best = 1e300;
+  int best_n = b->nstreams;
+  int rc = LGF_OK;
+  for (int ns : {4, 8, 16, 32}) {
+    if (ns > b->n && ns != 4) continue;
+    if ((rc = schedule(b, ns))) break;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = batch_stage(b, f_dev, phi_dev, nullptr, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(LGF_E_CUDA, "autotune stage failed");
+      float m = 0.f;
+      cudaEventElapsedTime(&m, e0, e1);
+      if (rep) ms = std::min(ms, m);
+    }
+    if (rc) break;
+    if (ms < best) best = ms, best_n = ns;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  return schedule(b, best_n);
+}
+
+int lgf_batch_tuning(const lgf_batch *b, int32_t *nstreams, int32_t *slices, double *ms) {
+  if (!b) return set_error(LGF_E_INVALID_ARG, "NULL batch");
+  if (nstreams) *nstreams = b->nstreams;
+  for (int i = 0; i < b->n; ++i) {
+    if (slices) slices[i] = b->opts_i[i].dft_slices;
+    if (ms) ms[i] = b->tuned_ms[i];
+  }
   return LGF_OK;
 }
 

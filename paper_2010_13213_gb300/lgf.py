@@ -102,6 +102,8 @@ def load():
         lib.lgf_batch_graph_create.argtypes = [c_void_p, c_int32, PP, PP, PP, PP, POINTER(c_double), c_void_p]
         lib.lgf_batch_graph_launch.argtypes = [c_void_p, c_void_p]
         lib.lgf_batch_graph_nodes.argtypes = [c_void_p, POINTER(c_int64)]
+        lib.lgf_batch_autotune.argtypes = [c_void_p, PP, PP, c_void_p]
+        lib.lgf_batch_tuning.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_double)]
         lib.lgf_device_status.argtypes = [c_void_p]
         lib.lgf_selftest_wait_timeout.argtypes = [c_void_p, c_int32, c_void_p]
         lib.lgf_last_error.restype = c_char_p
@@ -111,6 +113,7 @@ def load():
                      "lgf_refinement_indicator", "lgf_stage_projection", "lgf_batch_create",
                      "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
+                     "lgf_batch_autotune", "lgf_batch_tuning",
                      "lgf_device_status", "lgf_selftest_wait_timeout"):
             getattr(lib, name).restype = c_int32
         _LIB = lib
@@ -283,6 +286,20 @@ class Batch:
             flat = [float(a) for row in alpha_stages for a in row]
             al = (c_double * len(flat))(*flat)
         _check(load().lgf_batch_graph_create(c_void_p(self.h), int(nstages), f, p, g, t, al, c_void_p(cuda_stream)))
+
+    def autotune(self, f_ptrs, phi_ptrs, cuda_stream: int = 0):
+        f, _a = _ptrs(f_ptrs)
+        p, _b = _ptrs(phi_ptrs)
+        _check(load().lgf_batch_autotune(c_void_p(self.h), f, p, c_void_p(cuda_stream or None)))
+
+    def tuning(self):
+        """(stream count, per-instance digit slices, per-instance measured solve ms)."""
+        n = len(self.meshes)
+        ns = c_int32()
+        sl = (c_int32 * n)()
+        ms = (c_double * n)()
+        _check(load().lgf_batch_tuning(c_void_p(self.h), ctypes.byref(ns), sl, ms))
+        return ns.value, list(sl), list(ms)
 
     def graph_launch(self, cuda_stream: int):
         _check(load().lgf_batch_graph_launch(c_void_p(self.h), c_void_p(cuda_stream)))

@@ -191,3 +191,33 @@ def test_batch_rejects_mismatched_block_size(L, table8):
     with pytest.raises(L.LgfError) as e:
         L.Batch(table8, [m16], 1)
     assert e.value.status == L.LGF_E_MESH
+
+
+def test_batch_autotune_choices_and_results(L, table8, inst):
+    # the autotuner times each instance's DFT-pass variants and the stream counts; afterwards every stage
+    # reproduces the individual solves made with the chosen variant bit for bit, and stays within the
+    # DF32 accuracy of the untuned ones
+    b, meshes = make_batch(L, table8, inst)
+    fs = [torch.from_numpy(f).cuda() for _, f, _ in inst]
+    phis = [torch.zeros_like(f) for f in fs]
+    s = torch.cuda.Stream()
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    b.autotune(ptr(fs), ptr(phis), s.cuda_stream)
+    ns, slices, ms = b.tuning()
+    assert ns in (4, 8, 16, 32) and all(x in (0, 5) for x in slices) and all(m > 0 for m in ms)
+    b.graph_create(1, ptr(fs), ptr(phis), None, None, s.cuda_stream)
+    for t in phis:
+        t.zero_()
+    torch.cuda.synchronize()
+    b.graph_launch(s.cuda_stream)
+    torch.cuda.synchronize()
+    for i, (m, f) in enumerate(zip(meshes, fs)):
+        phi = torch.zeros_like(f)
+        L.lgf_poisson_solve(table8, m, 3, f.data_ptr(), phi.data_ptr(), L.LGF_F64,
+                            L.make_opts(precision=2, dft_slices=slices[i]))
+        ref = torch.zeros_like(f)
+        L.lgf_poisson_solve(table8, m, 3, f.data_ptr(), ref.data_ptr(), L.LGF_F64, L.make_opts(precision=2))
+        torch.cuda.synchronize()
+        assert torch.equal(phi, phis[i]), f"instance {i}"
+        assert (phi - ref).abs().max() <= 1e-10 * ref.abs().max()
+    b.close()

@@ -172,3 +172,45 @@ def test_mesh_errors(L, table8):
         assert e.value.status == L.LGF_E_TABLE_RANGE
     finally:
         L.lgf_table_destroy(small)
+
+
+def _reblock(mesh16, fields16):
+    """The same composite mesh with 8^3 blocks: block (bx, by, bz) of 16^3 cells -> its eight 8^3 sub-blocks;
+    fields [ncomp][nblk][16][16][16] -> [ncomp][8 nblk][8][8][8] in the matching order."""
+    sub = [(i, j, l) for l in (0, 1) for j in (0, 1) for i in (0, 1)]
+    levels8, f8 = [], []
+    for blk, f in zip(mesh16["levels"], fields16):
+        levels8.append(np.array([[2 * bx + i, 2 * by + j, 2 * bz + l] for bx, by, bz in blk for i, j, l in sub],
+                                np.int32))
+        out = np.zeros((f.shape[0], 8 * len(blk), 8, 8, 8))
+        for n in range(len(blk)):
+            for s, (i, j, l) in enumerate(sub):
+                out[:, 8 * n + s] = f[:, n, 8 * l:8 * l + 8, 8 * j:8 * j + 8, 8 * i:8 * i + 8]
+        f8.append(out)
+    return dict(B=8, h0=mesh16["h0"], n_ext=mesh16["n_ext"], levels=levels8), f8
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_results_do_not_depend_on_the_block_size(L, table8, precision):
+    # the regions Omega_k, Omega_k^E and the correction are defined on cells (n_ext in cells, whole-cell
+    # masks), so re-blocking the same composite mesh from 16^3 into 8^3 blocks changes only rounding
+    B = 16
+    lvl0 = S.box_blocks((48, 48, 32), B)
+    lvl1 = np.array([[2, 2, 1], [3, 2, 1], [2, 3, 1], [3, 3, 1], [2, 2, 2]], np.int32)
+    mesh16 = dict(B=B, h0=0.5, n_ext=6, levels=[lvl0, lvl1])
+    rng = np.random.default_rng(61)
+    f16 = [rng.standard_normal((2, len(b), B, B, B)) for b in mesh16["levels"]]
+    mesh8, f8 = _reblock(mesh16, f16)
+    t16 = L.lgf_table_create(16, (6, 6, 6), L.LGF_TBL_FP64 | L.LGF_TBL_DF32)
+    try:
+        got16, _ = gpu_solve(L, t16, mesh16, f16, precision)
+    finally:
+        L.lgf_table_destroy(t16)
+    got8, _ = gpu_solve(L, table8, mesh8, f8, precision)
+    back, _ = _reblock(mesh16, got16)  # express the B = 16 result in the 8^3 layout
+    for k in range(2):
+        a, b = back[k], got8[k]
+        m = np.isfinite(b)
+        assert (np.isfinite(a) == m).all()  # the same cells (Omega_k) written
+        scale = np.abs(b[m]).max()
+        assert np.abs(a[m] - b[m]).max() <= TOL[precision] * scale, k
