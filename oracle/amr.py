@@ -28,17 +28,20 @@ FLGF-AMR (Sec. 3.4, the three-step summary after Eq. (eq:AMR-LGF)):
 ``L_k^{-1} = h_k^2 G *`` is evaluated with a zero-padded FFT convolution over each level's box
 (a library primitive standing for the convolution sum of Sec. 2.2).
 
-FIF-AMR (Sec. 3.5, Eq. (eq:FIF-AMR)): ``g_k = Gamma_k E_{alpha_k} * (P_k fhat)`` where
-``P_k fhat = sum_i P_{i->k} fhat_i`` (Eq. (eq:interp)) and ``alpha_k = alpha_finest 4^{-(K-1-k)}``
-(Eq. (eq:composite-LGF-IF): the IF argument scales with 1/dx_k^2).
+FIF-AMR (Sec. 3.5, Eq. (eq:FIF-AMR)): ``g_k = Gamma_k E_{alpha_k} * (P_k fhat)`` where ``P_k fhat`` is the
+level-k reconstruction of the function the AMR data sample (Eq. (eq:interp): every region of the
+partition supplies the cells it holds, ``reconstruct``) and ``alpha_k = alpha_finest 4^{-(K-1-k)}``
+(Eq. (eq:composite-LGF-IF): the IF argument scales with 1/dx_k^2).  (In FLGF-AMR the coarse-to-fine
+operator acts on the partial solution psi_{k-1}, a function defined on the whole level, and on the
+sources only through the correction S, so its P is the plain interpolation of lattice functions.)
 
 Parity: K = 1 reduces to the single-level solve (pinned in ``core``); ``s_k = 0`` for linear psi;
 with n_ext -> infinity the result approaches the composite-grid definition
-``phi^k = L_k^{-1} sum_i P_{i->k} fhat_i`` evaluated directly (tests/test_oracle_amr.py).  FIF-AMR
-equals the heat definition ``E_{alpha_k} * sum_i P_{i->k} fhat_i`` (P composed per source level) on
-two and three levels, and both reproduce the lattice heat kernel's second moment
-``E_a * |n|^2 = |n|^2 + 6a``: the same physical increment ``6 kappa dt`` on every level pins the
-``4^{-(K-1-k)}`` scaling of alpha_k.
+``phi^k = L_k^{-1} sum_i P_{i->k} fhat_i`` evaluated directly (tests/test_oracle_amr.py).  The
+reconstruction reproduces linear functions exactly on every level (across level boundaries too);
+FIF-AMR keeps constants on every Omega_k cell away from the grid's outer boundary, and reproduces the
+lattice heat kernel's second moment ``E_a * |n|^2 = |n|^2 + 6a``: the same physical increment
+``6 kappa dt`` on every level pins the ``4^{-(K-1-k)}`` scaling of alpha_k.
 """
 from __future__ import annotations
 
@@ -49,8 +52,8 @@ import scipy.fft as sfft
 
 from . import core
 
-__all__ = ["Level", "build_levels", "flgf_amr", "fif_amr", "composite_definition", "composite_heat_definition",
-           "interp_up", "coarsen", "dilate_maxnorm", "laplacian_box", "solve_level_box"]
+__all__ = ["Level", "build_levels", "flgf_amr", "fif_amr", "composite_definition", "reconstruct", "interp_up",
+           "coarsen", "dilate_maxnorm", "laplacian_box", "solve_level_box"]
 
 
 class Level:
@@ -297,64 +300,44 @@ def composite_definition(mesh, f_levels):
     return out
 
 
-def composite_heat_definition(mesh, f_levels, alpha_finest):
-    """The composite-grid definition of the heat apply (Eqs. (eq:interp), (eq:FIF-AMR)):
-    ``g_k = E_{alpha_k} * (sum_i P_{i->k} fhat_i)`` restricted to Omega_k, every P applied to the whole
-    (compact) source of level i and composed level by level (Eq. (eq:P_composition)), the sum formed on
-    the full level box and convolved there (no region cut), ``alpha_k = alpha_finest 4^{-(K-1-k)}``
-    (Eq. (eq:composite-LGF-IF): the argument kappa dt / dx_k^2 on a level of spacing dx_k)."""
-    B = mesh["B"]
-    blocks = mesh["levels"]
-    K = len(blocks)
-    lv = build_levels(mesh, pad_extra=8)
-    fhat = [_user_field(lv[k], blocks[k], f_levels[k], B) for k in range(K)]
-    out = []
-    for k in range(K):
-        tot = fhat[k].copy()
-        for i in range(k):
-            u = fhat[i]
-            for j in range(i + 1, k + 1):
-                u = np.nan_to_num(interp_up(u, lv[j - 1], lv[j]), nan=0.0)
-            tot = tot + u
-        for i in range(k + 1, K):
-            u = fhat[i]
-            for j in range(i - 1, k - 1, -1):
-                u = coarsen(u, lv[j + 1], lv[j])
-            tot = tot + u
-        dx_ratio = 2.0 ** (K - 1 - k)  # dx_k / dx_finest
-        g = core.heat_box(tot, alpha_finest / dx_ratio ** 2)
-        g = np.where(lv[k].omega[None], g, 0.0)
-        out.append(_to_blocks(lv[k], blocks[k], g, B))
-    return out
+def reconstruct(lv, fhat):
+    """P_k fhat on every level box (Sec. 3.2, Eq. (eq:interp)): the level-k information of the function the
+    AMR data sample.  ``fhat[k]`` is [ncomp][box_k], zero off Omega_k.  The regions partition space
+    (Eq. (eq:partition)), so every level-k cell takes its value from the one region that holds it:
+    * cells of the level-k blocks: F_k = fhat_k + P_{k+1->k} F_{k+1}, i.e. own values on Omega_k and the
+      8-child means of the finer levels on covered cells (cumulative coarsening);
+    * every other cell: P_{k-1->k} of the level-(k-1) reconstruction, which itself holds the coarsened
+      level-k data on its covered cells, so the interpolation near a level boundary reads values of the
+      same function on both sides.
+    Constants and linear functions are reproduced exactly wherever the stencils stay inside the grid."""
+    K = len(lv)
+    F = [None] * K
+    F[K - 1] = fhat[K - 1]
+    for k in range(K - 2, -1, -1):
+        F[k] = fhat[k] + coarsen(F[k + 1], lv[k + 1], lv[k])
+    T = [F[0]]
+    for k in range(1, K):
+        up = interp_up(T[k - 1], lv[k - 1], lv[k])
+        T.append(np.where(lv[k].user[None], F[k], up))
+    return T
 
 
 def fif_amr(mesh, f_levels, alpha_finest, r=None):
     """FIF-AMR heat apply (Sec. 3.5, Eq. (eq:FIF-AMR)): ``g_k = Gamma_k E_{alpha_k} * (P_k fhat)``.
 
-    ``P_k fhat = sum_i P_{i->k} fhat_i`` is built as the cumulative coarsening F_k (own and finer
-    levels) plus the cumulative interpolation of the coarser levels,
-    ``U_0 = fhat_0, U_k = fhat_k + P_{k-1->k} U_{k-1}``, i.e. ``P_k fhat = F_k + P_{k-1->k} U_{k-1}``.
-    The level-k kernel argument is ``alpha_k = alpha_finest * 4^{-(K-1-k)}``.
+    ``P_k fhat`` is the level-k reconstruction of the AMR data (``reconstruct``: own values on Omega_k,
+    8-child means of the finer levels on covered cells, interpolation of the coarser level's reconstruction
+    elsewhere).  The level-k kernel argument is ``alpha_k = alpha_finest * 4^{-(K-1-k)}``.
     """
     B = mesh["B"]
     blocks = mesh["levels"]
     K = len(blocks)
     lv = build_levels(mesh)
     fhat = [_user_field(lv[k], blocks[k], f_levels[k], B) for k in range(K)]
-    F = [None] * K
-    F[K - 1] = fhat[K - 1]
-    for k in range(K - 2, -1, -1):
-        F[k] = fhat[k] + coarsen(F[k + 1], lv[k + 1], lv[k])
-    U = [None] * K
+    T = reconstruct(lv, fhat)
     out = []
     for k in range(K):
-        if k == 0:
-            Pf = F[0]
-            U[0] = fhat[0]
-        else:
-            up = interp_up(U[k - 1], lv[k - 1], lv[k])
-            Pf = F[k] + up
-            U[k] = fhat[k] + up
+        Pf = T[k]
         alpha_k = alpha_finest * 4.0 ** (-(K - 1 - k))
         Kh, rr = core.heat_kernel_full(alpha_k, r)
         region = dilate_maxnorm(lv[k].omega, rr)

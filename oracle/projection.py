@@ -12,10 +12,11 @@ D = -G^T and D G = L_C, the 7-point Laplacian (Eq. (eq:mimetic)).  A stage solve
 
 On the AMR grid (readings of Sec. 3.6, which leaves the transfer of face data open):
 * r^ is given on the caller's blocks of every level; only its values on Omega_k are used;
-* D^r on Omega_k is D applied to the level-k reconstruction P_k r^ = sum_i P_{i->k} r^_i (own values,
-  interpolation of coarser levels, 8-child means of finer ones, every component treated as a cell-centred
-  scalar); the faces just outside Omega_k take their values from the neighbouring regions through it (the
-  one-cell-larger restriction of Sec. 3.6);
+* D^r on Omega_k is D applied to the level-k reconstruction P_k r^ (``amr.reconstruct``: own values on
+  Omega_k, 8-child means of the finer levels on covered cells, interpolation of the coarser level's
+  reconstruction elsewhere; every component treated as a cell-centred scalar); the faces just outside
+  Omega_k take their values from the neighbouring regions through it (the one-cell-larger restriction of
+  Sec. 3.6);
 * p^ = FLGF-AMR(D^r) on Omega_k (``amr.flgf_amr``);
 * G^p on the faces of the Omega_k cells is G applied to the reconstruction P_k p^;
 * u^ = FIF-AMR(r^ - G^p) (``amr.fif_amr``) with the caller's alpha for the finest level.
@@ -62,27 +63,6 @@ def gradient(p, h):
     return out
 
 
-def reconstruct(mesh, lv, fields):
-    """P_k f^ = sum_i P_{i->k} f^_i on every level box (Eq. (eq:interp)): ``fields[k]`` is [ncomp][box_k]
-    zero off Omega_k; coarser levels interpolated level by level, finer ones coarsened level by level."""
-    K = len(lv)
-    out = []
-    for k in range(K):
-        tot = fields[k].copy()
-        for i in range(k):
-            u = fields[i]
-            for j in range(i + 1, k + 1):
-                u = np.nan_to_num(amr.interp_up(u, lv[j - 1], lv[j]), nan=0.0)
-            tot = tot + u
-        for i in range(k + 1, K):
-            u = fields[i]
-            for j in range(i - 1, k - 1, -1):
-                u = amr.coarsen(u, lv[j + 1], lv[j])
-            tot = tot + u
-        out.append(tot)
-    return out
-
-
 def _to_box(lv, blocks, data, B):
     out = np.zeros((data.shape[0],) + lv.shape)
     for i, b in enumerate(blocks):
@@ -105,11 +85,11 @@ def project_amr(mesh, r_levels, alpha_finest, return_internals=False):
     blocks = mesh["levels"]
     K = len(blocks)
     lv = amr.build_levels(mesh)
-    rr = reconstruct(mesh, lv, [_to_box(lv[k], blocks[k], r_levels[k], B) for k in range(K)])
+    rr = amr.reconstruct(lv, [_to_box(lv[k], blocks[k], r_levels[k], B) for k in range(K)])
     d = [np.where(lv[k].omega, divergence(rr[k], lv[k].h), 0.0)[None] for k in range(K)]
     d_blk = [_to_blocks(lv[k], blocks[k], d[k], B) for k in range(K)]
     p_blk, _ = amr.flgf_amr(mesh, d_blk)
-    pp = reconstruct(mesh, lv, [_to_box(lv[k], blocks[k], p_blk[k], B) for k in range(K)])
+    pp = amr.reconstruct(lv, [_to_box(lv[k], blocks[k], p_blk[k], B) for k in range(K)])
     w_blk = []
     for k in range(K):
         w = np.where(lv[k].omega[None], rr[k] - gradient(pp[k][0], lv[k].h), 0.0)

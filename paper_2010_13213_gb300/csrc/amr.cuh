@@ -283,29 +283,26 @@ struct HeatW {
   int r;
 };
 
-// U_k = [OM] fhat_k + P U_{k-1} (k >= 1), or S_k = F_k + P U_{k-1}; grid (|HB_k|, ncomp).
-// mode 0: out = [OM] fhat (+ P U_{k-1});  mode 1: out = F (+ P U_{k-1})
+// P_k fhat, the level-k reconstruction of the AMR data (Sec. 3.2, Eq. (eq:interp)); grid (|HB_k|, ncomp).
+// The regions partition space, so each cell takes the value of the region that holds it: on the caller's
+// level-k blocks F_k (own values on Omega_k, 8-child means of the finer levels on covered cells); on every
+// other block the interpolation of the level-(k-1) reconstruction Uc (which holds the coarsened level-k data
+// on its covered cells, so interpolation next to a level boundary reads the same function on both sides).
 template <class R>
-__global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *blocks, const int32_t *HB, int mode,
-                                                    const void *f_user, int dtype, int64_t ucs, const R *F,
+__global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *blocks, const int32_t *HB, const R *F,
                                                     int nU, R *out, int64_t cs, LevelDev Lc, const R *Uc,
                                                     int64_t ucs_c, int has_coarse) {
   const int b = HB[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
-  const int u = L.user_of[b];
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     R v = RT<R>::zero();
-    if (mode == 0) {
-      if ((L.cellmask[(int64_t)b * B3 + off] & 1) && u >= 0)
-        v = load_field<R>(f_user, comp * ucs + (int64_t)u * B3 + off, dtype);
-    } else if (b < nU) {
+    if (b < nU) {
       v = F[comp * cs + (int64_t)b * B3 + off];
-    }
-    if (has_coarse) {
+    } else if (has_coarse) {
       const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
                 z = (bc.z << sh) + (off >> (2 * sh));
-      v = v + interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, Uc, ucs_c, comp, i, j, k); });
+      v = interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, Uc, ucs_c, comp, i, j, k); });
     }
     out[comp * cs + (int64_t)b * B3 + off] = v;
   }

@@ -589,18 +589,14 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
     const size_t bytes = sizeof(R) * (size_t)ncomp * L.BL.size() * B3;
     cudaMemsetAsync(T0, 0, bytes, st);
     cudaMemsetAsync(T1, 0, bytes, st);
-    if (k + 1 < K) {
-      cudaMemsetAsync(Ucur, 0, bytes, st);
-      k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 0, f, dtype, ucs, Fall + Foff[k], L.nU, Ucur,
-                                                        cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
-      LGF_LAUNCH_CHECK("heat U");
-    }
-    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 1, f, dtype, ucs, Fall + Foff[k], L.nU, T0,
-                                                      cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
+    cudaMemsetAsync(Ucur, 0, bytes, st);
+    // P_k fhat into Ucur: the heat passes' source, kept for the next level's interpolation
+    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, Fall + Foff[k], L.nU, Ucur, cs[k], Lc, Uprev,
+                                                      k > 0 ? cs[k - 1] : 0, k > 0);
     LGF_LAUNCH_CHECK("heat source");
     tm.mark(PH_INTERP);
-    for (int ax = 0; ax < 3; ++ax) {  // x: T0 -> T1, y: T1 -> T0, z: T0 -> T1
-      const R *hin = ax == 1 ? T1 : T0;
+    for (int ax = 0; ax < 3; ++ax) {  // x: Ucur -> T1, y: T1 -> T0, z: T0 -> T1
+      const R *hin = ax == 0 ? Ucur : (ax == 1 ? T1 : T0);
       R *hout = ax == 1 ? T0 : T1;
       if ((rc = heat_pass_launch<R>(B, Ld, L.d_BL, HB, nHB, ncomp, ax, hin, hout, cs[k], W[k], st))) return rc;
       ++launches;
@@ -691,10 +687,10 @@ static int reconstruct_levels(Plan *P, const lgf_mesh *m, int ncomp, const void 
   }
   const size_t field = sizeof(R) * (size_t)ncomp * maxBL * B3;
   int rc;
-  if ((rc = ws->buf[10].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[11].reserve(field)) ||
-      (rc = ws->buf[13].reserve(field)) || (rc = ws->buf[14].reserve(field)))
+  if ((rc = ws->buf[10].reserve(sizeof(R) * (size_t)Foff[K])) || (rc = ws->buf[13].reserve(field)) ||
+      (rc = ws->buf[14].reserve(field)))
     return rc;
-  R *Fall = (R *)ws->buf[10].p, *T = (R *)ws->buf[11].p, *Uprev = (R *)ws->buf[13].p, *Ucur = (R *)ws->buf[14].p;
+  R *Fall = (R *)ws->buf[10].p, *Uprev = (R *)ws->buf[13].p, *Ucur = (R *)ws->buf[14].p;
   for (int k = K - 1; k >= 0; --k) {
     const LevelPlan &L = P->L[k];
     const LevelDev Ld = level_dev(P, k, m->h0);
@@ -714,17 +710,11 @@ static int reconstruct_levels(Plan *P, const lgf_mesh *m, int ncomp, const void 
     const int nHB = (int)L.HB.size();
     const int32_t *HB = L.d_lists + L.off_HB;
     const size_t bytes = sizeof(R) * (size_t)ncomp * L.BL.size() * B3;
-    cudaMemsetAsync(T, 0, bytes, st);
-    if (k + 1 < K) {
-      cudaMemsetAsync(Ucur, 0, bytes, st);
-      k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 0, f, dtype, ucs, Fall + Foff[k], L.nU, Ucur,
-                                                        cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
-      LGF_LAUNCH_CHECK("reconstruction U");
-    }
-    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, 1, f, dtype, ucs, Fall + Foff[k], L.nU, T,
-                                                      cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
+    cudaMemsetAsync(Ucur, 0, bytes, st);
+    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, Fall + Foff[k], L.nU, Ucur, cs[k], Lc, Uprev,
+                                                      k > 0 ? cs[k - 1] : 0, k > 0);
     LGF_LAUNCH_CHECK("reconstruction");
-    if ((rc = consume(k, Ld, (const R *)T, cs[k]))) return rc;
+    if ((rc = consume(k, Ld, (const R *)Ucur, cs[k]))) return rc;
     ++launches;
     std::swap(Uprev, Ucur);
   }
