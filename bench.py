@@ -270,6 +270,13 @@ def batch_poisson(L, torch, dev, steps, warmup, world, pk, fp64=True, check=True
         if name == "fp64" and not fp64:
             continue
         b = L.Batch(table, meshes, 3, L.LGF_F64, opts=L.make_opts(precision=prec), nstreams=nstreams)
+        t0 = time.perf_counter()
+        b.autotune(ptr(fs), ptr(phis), bs.cuda_stream)  # measured DFT-pass variant, order and stream count
+        ns, slices, tuned_ms = b.tuning()
+        res[name + "_tuning"] = {"nstreams": ns, "tensor_core_instances": int(sum(1 for x in slices if x)),
+                                 "slices": sorted(set(slices)), "autotune_s": time.perf_counter() - t0,
+                                 "instance_ms_sum": float(sum(tuned_ms)),
+                                 "instance_ms_max": float(max(tuned_ms))}
         b.graph_create(1, ptr(fs), ptr(phis), None, None, bs.cuda_stream)
         nsteps = steps if name == "df32" else max(2, min(steps, 5))
         ms = time_calls(torch, lambda: b.graph_launch(bs.cuda_stream), nsteps, warmup, bs, world=world)
@@ -604,7 +611,8 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_df, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances": NINST, "blocks": hb["blocks"], "target_cells": total,
-                       "ncomp": 3, "nstreams": hb["nstreams"], "graph_nodes": res["df32"]["nodes"],
+                       "ncomp": 3, "graph_nodes": res["df32"]["nodes"],
+                       "autotune": {"df32": res["df32_tuning"], "fp64": res.get("fp64_tuning")},
                        "parallelism": f"replicas{world}",
                        "l2": "no flush: the 64 instances' fields (about 1.7 GB of sources, as much of results) are "
                              "larger than L2"},
