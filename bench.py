@@ -548,6 +548,103 @@ def bump_study(L, torch, dev):
     return out
 
 
+def projection_line(L, torch, dev, steps, warmup, world, flush):
+    """HERK stage projection L_C p = D r, u = H(r - G p) (Sec. 2.4, Sec. 3.6) in DF32 on the three-level ring
+    mesh (the ring vorticity as the face field r, alpha_finest = 0.1): time per call (L2 flushed between
+    calls), and the error against the oracle's projection on the small three-level ring (8^3 blocks)."""
+    import lgf_synth as S
+    from oracle import projection
+    out = {}
+    small, fs = S.three_level_ring(R=1.0, sigma=0.2, B=8, n_ext=6, h_fine=1 / 32, support=(24, 24, 16), dilate0=1)
+    ref_u, ref_p = projection.project_amr(small, fs, 0.1)
+    t8 = L.lgf_table_create(8, (14, 14, 14), L.LGF_TBL_BOX_ONLY)
+    m8 = L.Mesh(small["levels"], 8, small["h0"], n_ext=small["n_ext"])
+    r8 = torch.from_numpy(np.concatenate(fs, axis=1)).to(dev)
+    u8 = torch.zeros_like(r8)
+    p8 = torch.zeros((1,) + tuple(r8.shape[1:]), dtype=torch.float64, device=dev)
+    L.lgf_stage_projection(t8, m8, r8.data_ptr(), u8.data_ptr(), p8.data_ptr(), L.LGF_F64, 0.1,
+                           L.make_opts(precision=L.LGF_PREC_DF32, mac_mode=L.LGF_MAC_BOX))
+    torch.cuda.synchronize()
+    gu, gp = u8.cpu().numpy(), p8.cpu().numpy()
+    lv_masks = projection.amr.build_levels(small)
+    err, o = 0.0, 0
+    for k, blk in enumerate(small["levels"]):
+        msk = projection._to_blocks(lv_masks[k], blk, lv_masks[k].omega[None].astype(float), 8)[0] > 0.5
+        for got, ref in ((gu[:, o:o + len(blk)], ref_u[k]), (gp[:, o:o + len(blk)], ref_p[k])):
+            if msk.any():
+                err = max(err, float(np.abs(got[:, msk] - ref[:, msk]).max() / np.abs(ref[:, msk]).max()))
+        o += len(blk)
+    L.lgf_table_destroy(t8)
+    mesh, f = S.three_level_ring()
+    m = L.Mesh(mesh["levels"], 16, mesh["h0"], n_ext=mesh["n_ext"])
+    table = L.lgf_table_create(16, (14, 14, 14), L.LGF_TBL_BOX_ONLY)
+    r = torch.from_numpy(np.concatenate(f, axis=1)).to(dev)
+    u = torch.zeros_like(r)
+    st = torch.cuda.Stream(dev)
+    opts = L.make_opts(precision=L.LGF_PREC_DF32, mac_mode=L.LGF_MAC_BOX)
+    call = lambda: L.lgf_stage_projection(table, m, r.data_ptr(), u.data_ptr(), 0, L.LGF_F64, 0.1, opts, None,
+                                          st.cuda_stream)
+    ms = time_calls(torch, call, steps, warmup, st, flush=flush, world=world)
+    rep = L.lgf_report()
+    L.lgf_stage_projection(table, m, r.data_ptr(), u.data_ptr(), 0, L.LGF_F64, 0.1, opts, rep, st.cuda_stream)
+    torch.cuda.synchronize()
+    L.lgf_table_destroy(table)
+    cells = int(rep.target_cells)
+    return {"workload": "three-level ring mesh (h = R/16, R/32, R/64, 16^3 blocks), the ring vorticity as r, "
+                        "alpha_finest = 0.1, DF32", "ms_per_step": ms, "value": cells / (ms * 1e-3) / 1e6,
+            "unit": "Mcells/s", "target_cells": cells, "gpu_launches": int(rep.kernel_launches),
+            "rel_err": err, "rel_err_case": "small three-level ring (8^3 blocks), u and p against the oracle",
+            "l2": "flushed by a 256 MiB write between timed calls (outside the events)"}
+
+
+def indicator_line(L, torch, dev, steps, warmup, world, flush):
+    """Refinement indicator (Sec. 4.2) computed with the DF32 solve of the three-level ring: the time of the
+    solve with the indicator against the solve alone, and the agreement with the oracle (block RMS, flags)
+    on the same mesh."""
+    import lgf_synth as S
+    from oracle import refine
+    mesh, f = S.three_level_ring()
+    m = L.Mesh(mesh["levels"], 16, mesh["h0"], n_ext=mesh["n_ext"])
+    table = L.lgf_table_create(16, (14, 14, 14), L.LGF_TBL_BOX_ONLY)
+    ft = torch.from_numpy(np.concatenate(f, axis=1)).to(dev)
+    phi = torch.zeros_like(ft)
+    n = m.total_blocks
+    rms = torch.zeros(n, dtype=torch.float64, device=dev)
+    flags = torch.zeros(n, dtype=torch.uint8, device=dev)
+    smax = torch.zeros(1, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream(dev)
+    opts = L.make_opts(precision=L.LGF_PREC_DF32, mac_mode=L.LGF_MAC_BOX)
+
+    def with_ind():
+        smax.zero_()
+        L.lgf_refinement_indicator(table, m, 3, ft.data_ptr(), phi.data_ptr(), L.LGF_F64, opts, 0.3, 0.5, 2,
+                                   rms.data_ptr(), flags.data_ptr(), smax.data_ptr(), None, st.cuda_stream)
+
+    def plain():
+        L.lgf_poisson_solve(table, m, 3, ft.data_ptr(), phi.data_ptr(), L.LGF_F64, opts, None, st.cuda_stream)
+
+    ms_ind = time_calls(torch, with_ind, steps, warmup, st, flush=flush, world=world)
+    ms_plain = time_calls(torch, plain, steps, warmup, st, flush=flush, world=world)
+    with torch.cuda.stream(st):
+        with_ind()
+    torch.cuda.synchronize()
+    ref = refine.refinement_indicator(mesh, f, 0.3, 0.5, 2)
+    got_rms, got_fl = rms.cpu().numpy(), flags.cpu().numpy()
+    scale = max(r.max() for r in ref["rms"])
+    rms_err, flag_miss, o = 0.0, 0, 0
+    for k, blk in enumerate(mesh["levels"]):
+        rms_err = max(rms_err, float(np.abs(got_rms[o:o + len(blk)] - ref["rms"][k]).max() / scale))
+        flag_miss += int(((got_fl[o:o + len(blk)] & 1) > 0).tolist() != ref["refine"][k].tolist())
+        flag_miss += int(((got_fl[o:o + len(blk)] & 2) > 0).tolist() != ref["coarsen"][k].tolist())
+        o += len(blk)
+    L.lgf_table_destroy(table)
+    return {"workload": "three-level ring, DF32 solve + indicator (alpha = 0.3, beta = 0.5, N_l = 2)",
+            "ms_solve_with_indicator": ms_ind, "ms_solve_alone": ms_plain, "overhead": ms_ind / ms_plain - 1.0,
+            "rms_rel_err": rms_err, "flag_levels_differing": flag_miss,
+            "refine_blocks": int(((got_fl & 1) > 0).sum()), "coarsen_blocks": int(((got_fl & 2) > 0).sum()),
+            "s_max": float(smax.item())}
+
+
 def cfg2_case():
     import lgf_synth as S
     case = S.single_level_ring()
@@ -602,6 +699,8 @@ def run_gpu(args):
         extra["heat_apply"] = heat_line(L, torch, dev, 10, 3, world, pk, flush)
         extra["velocity_refresh"] = refresh_line(L, torch, dev, 10, 3, world, flush)
         extra["bump_study"] = bump_study(L, torch, dev)
+        extra["stage_projection"] = projection_line(L, torch, dev, 10, 3, world, flush)
+        extra["refinement_indicator"] = indicator_line(L, torch, dev, 10, 3, world, flush)
     if rank == 0:
         total = hb["total"]
         mid_ms = hb["mid_ms"]
