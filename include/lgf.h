@@ -154,6 +154,17 @@ typedef struct lgf_report {
 int lgf_table_create(lgf_table **out, int32_t block, const int32_t max_block_offset[3],
                      uint32_t flags, void *cuda_stream);
 
+/*
+ * lgf_table_prepare -- build everything a Poisson solve of mesh m on cuda_stream uses (the cached plan of
+ * the mesh, the block-index FFT spectra of each level's box shape, the stream's workspace for ncomp
+ * components of the given storage type and opts->precision / mac_mode) by one solve of a zero source into
+ * trial fields it allocates and frees.  Afterwards solves of that mesh with those options on that stream
+ * allocate nothing and only read the table (so solves on different streams, each prepared, may run
+ * concurrently); without it the first solve does this work.  Synchronises cuda_stream.
+ */
+int lgf_table_prepare(lgf_table *t, const lgf_mesh *m, int32_t ncomp, int32_t dtype, const lgf_solve_opts *opts,
+                      void *cuda_stream);
+
 /* lgf_table_destroy -- release a table and every workspace it holds (synchronises the device). */
 int lgf_table_destroy(lgf_table *t);
 

@@ -266,6 +266,36 @@ int lgf_refinement_indicator(lgf_table *t, const lgf_mesh *m, int32_t ncomp, con
   return solve_multi(t, m, ncomp, f_dev, phi_dev, dtype, o, rep, (cudaStream_t)cuda_stream, ind);
 }
 
+int lgf_table_prepare(lgf_table *t, const lgf_mesh *m, int32_t ncomp, int32_t dtype, const lgf_solve_opts *opts,
+                      void *cuda_stream) {
+  if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");
+  int rc = check_mesh(m, t->B);
+  if (rc) return rc;
+  if (ncomp < 1) return set_error(LGF_E_INVALID_ARG, "ncomp %d", ncomp);
+  if (dtype != LGF_F64 && dtype != LGF_F32) return set_error(LGF_E_INVALID_ARG, "dtype %d", dtype);
+  int64_t nblk = 0;
+  for (int k = 0; k < m->nlevels; ++k) nblk += m->nblocks[k];
+  const size_t bytes = (size_t)ncomp * nblk * t->B * t->B * t->B * (dtype == LGF_F32 ? 4 : 8);
+  void *f = nullptr, *phi = nullptr;
+  if (cudaMalloc(&f, bytes) != cudaSuccess || cudaMalloc(&phi, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(f);
+    return set_error(LGF_E_OOM, "prepare: %zu bytes of trial fields", bytes);
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaMemsetAsync(f, 0, bytes, st);
+  lgf_solve_opts o{LGF_PREC_FP64, LGF_MAC_AUTO, 0, 0, 0.0, 0, 0};
+  if (opts) o = *opts;
+  o.timing = 0;
+  o.residual = 0;
+  rc = lgf_poisson_solve(t, m, ncomp, f, phi, dtype, &o, nullptr, cuda_stream);  // builds and caches
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(f);
+  cudaFree(phi);
+  if (rc) return rc;
+  return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "prepare: %s", cudaGetErrorString(e));
+}
+
 int lgf_stage_projection(lgf_table *t, const lgf_mesh *m, const void *r_dev, void *u_dev, void *p_dev, int32_t dtype,
                          double alpha_finest, const lgf_solve_opts *opts, lgf_report *rep, void *cuda_stream) {
   if (!t) return set_error(LGF_E_INVALID_ARG, "table is NULL");

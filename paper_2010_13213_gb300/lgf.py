@@ -89,6 +89,8 @@ def load():
                                                  c_int32, c_int32, c_void_p]
         lib.lgf_velocity_refresh.argtypes = [c_void_p, POINTER(lgf_mesh), c_void_p, c_void_p, c_int32,
                                              POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
+        lib.lgf_table_prepare.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_int32, POINTER(lgf_solve_opts),
+                                          c_void_p]
         lib.lgf_stage_projection.argtypes = [c_void_p, POINTER(lgf_mesh), c_void_p, c_void_p, c_void_p, c_int32,
                                              c_double, POINTER(lgf_solve_opts), POINTER(lgf_report), c_void_p]
         lib.lgf_refinement_indicator.argtypes = [c_void_p, POINTER(lgf_mesh), c_int32, c_void_p, c_void_p, c_int32,
@@ -110,7 +112,7 @@ def load():
         lib.lgf_version.restype = c_char_p
         for name in ("lgf_table_create", "lgf_table_destroy", "lgf_table_lgf_values", "lgf_poisson_solve",
                      "lgf_heat_apply", "lgf_poisson_solve_static", "lgf_velocity_refresh",
-                     "lgf_refinement_indicator", "lgf_stage_projection", "lgf_batch_create",
+                     "lgf_refinement_indicator", "lgf_stage_projection", "lgf_table_prepare", "lgf_batch_create",
                      "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
                      "lgf_batch_autotune", "lgf_batch_tuning",
@@ -158,6 +160,12 @@ def lgf_table_create(block: int, max_block_offset, flags: int = LGF_TBL_FP64, cu
     mo = (c_int32 * 3)(*[int(v) for v in max_block_offset])
     _check(load().lgf_table_create(ctypes.byref(h), int(block), mo, int(flags), c_void_p(cuda_stream or None)))
     return h.value
+
+
+def lgf_table_prepare(table, mesh: Mesh, ncomp: int, dtype: int = LGF_F64, opts: lgf_solve_opts | None = None,
+                      cuda_stream: int = 0) -> None:
+    _check(load().lgf_table_prepare(c_void_p(table), ctypes.byref(mesh.c), int(ncomp), int(dtype),
+                                    ctypes.byref(opts) if opts is not None else None, c_void_p(cuda_stream or None)))
 
 
 def lgf_table_destroy(table) -> None:

@@ -151,3 +151,32 @@ def test_ring_96x96x48_full_field_and_samples(L, table16, ring_case, precision):
     for c in range(2):
         sample = got[c][idx[:, 2], idx[:, 1], idx[:, 0]]
         assert np.abs(sample - direct[c]).max() <= TOL[precision] * np.abs(ref[c]).max()
+
+
+def test_prepared_table_allocates_nothing_during_solves(L):
+    # after lgf_table_prepare the solve builds nothing: the report's workspace stays the same, and a CUDA
+    # graph capture of the solve (which forbids allocation) succeeds
+    import lgf_synth as S2
+    case = S2.single_level_ring()
+    mesh = L.Mesh([case["blocks"]], 16, case["h"])
+    t = L.lgf_table_create(16, (5, 5, 2), L.LGF_TBL_BOX_ONLY)
+    try:
+        s = torch.cuda.Stream()
+        opts = L.make_opts(precision=L.LGF_PREC_DF32)
+        L.lgf_table_prepare(t, mesh, 3, L.LGF_F64, opts, s.cuda_stream)
+        f = torch.from_numpy(case["f"]).cuda()
+        phi = torch.zeros_like(f)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            L.lgf_poisson_solve(t, mesh, 3, f.data_ptr(), phi.data_ptr(), L.LGF_F64, opts, None, s.cuda_stream)
+            g.capture_end()
+        g.replay()
+        torch.cuda.synchronize()
+        ref = torch.zeros_like(f)
+        L.lgf_poisson_solve(t, mesh, 3, f.data_ptr(), ref.data_ptr(), L.LGF_F64, opts)
+        torch.cuda.synchronize()
+        assert torch.equal(phi, ref)
+    finally:
+        L.lgf_table_destroy(t)
