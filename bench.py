@@ -393,8 +393,23 @@ def single_config(L, torch, dev, name, case, steps, warmup, world, pk, precision
     f = torch.from_numpy(case["f"]).to(dev)
     phi = torch.zeros_like(f)
     st = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
     ref = oracle.solve_box_fft(case["box"], case["h"])
-    out = {"cells": cells, "ncomp": ncomp, "blocks": int(len(case["blocks"]))}
+    cpu_s = time.perf_counter() - t0
+    out = {"cells": cells, "ncomp": ncomp, "blocks": int(len(case["blocks"])),
+           "cpu_oracle": {"value": cells / cpu_s / 1e6, "unit": "Mcells/s", "cores": os.cpu_count(),
+                          "kind": "oracle", "sample": "the whole configuration once: zero-padded FP64 FFT "
+                                                      "convolution (pocketfft)"}}
+    if name == "cfg1":  # the direct O(N^2) sum on a seeded sample of target cells, extrapolated
+        rng = np.random.default_rng(7)
+        nz, ny, nx = case["shape"]
+        tg = np.stack([rng.integers(0, nx, 512), rng.integers(0, ny, 512), rng.integers(0, nz, 512)], 1)
+        t0 = time.perf_counter()
+        oracle.solve_box_direct(case["box"], case["h"], tg)
+        dt = time.perf_counter() - t0
+        out["cpu_oracle_direct"] = {"value": 512 / dt / 1e6, "unit": "Mcells/s (targets)", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": "512 seeded target cells of the 32^3 box, the "
+                                                                "compensated direct sum over all 32768 sources"}
     variants = [(n, p, 0) for n, p in precisions] + [(f"df32_tc{s}", L.LGF_PREC_DF32, s) for s in slices]
     for vname, prec, sl in variants:
         opts = L.make_opts(precision=prec, mac_mode=mode, dft_slices=sl)
@@ -424,13 +439,18 @@ def multi_config(L, torch, dev, steps, warmup, world, pk, flush):
     import lgf_synth as S
     from oracle import amr
     mesh, f = S.three_level_ring()
+    t0 = time.perf_counter()
     ref, masks = amr.flgf_amr(mesh, f)
+    cpu_s = time.perf_counter() - t0
     m = L.Mesh(mesh["levels"], mesh["B"], mesh["h0"], n_ext=mesh["n_ext"])
     ft = torch.from_numpy(np.concatenate(f, axis=1)).to(dev)
     phi = torch.zeros_like(ft)
     table = L.lgf_table_create(16, (14, 14, 14), L.LGF_TBL_BOX_ONLY)
     st = torch.cuda.Stream(dev)
-    out = {"levels": [len(b) for b in mesh["levels"]]}
+    ncells = int(sum(int(mk.sum()) for mk in masks))
+    out = {"levels": [len(b) for b in mesh["levels"]],
+           "cpu_oracle": {"value": ncells / cpu_s / 1e6, "unit": "Mcells/s", "cores": os.cpu_count(),
+                          "kind": "oracle", "sample": "the whole configuration once: the FP64 FLGF-AMR oracle"}}
     for vname, prec in (("df32", L.LGF_PREC_DF32), ("fp64", L.LGF_PREC_FP64), ("fp32", L.LGF_PREC_FP32)):
         rep = L.lgf_report()
         call = lambda: L.lgf_poisson_solve(table, m, 3, ft.data_ptr(), phi.data_ptr(), L.LGF_F64,

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "box.cuh"
+#include "box_fft.cuh"
 #include "box_tc.cuh"
 #include "internal.h"
 
@@ -121,6 +122,41 @@ static int tc_pass(int slices, const cx<R> *in, cx<R> *out, int64_t fstride, con
   return set_error(LGF_E_INVALID_ARG, "%d DFT-GEMM slices are not available for this precision", slices);
 }
 
+// Launch of the FFT passes for a block count 9..16; false for any other count.
+template <class R, int B, int NT>
+static bool bfft_fwd(int nb, const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
+                     const BoxTw<R> &tw, int gather, int n, int lines, const FwdSpecs &sp, cudaStream_t st) {
+  const dim3 grid(B * B * B / NT, lines, n);
+  switch (nb) {
+    case 9: k_bfft_fwd<R, B, NT, 9><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 10: k_bfft_fwd<R, B, NT, 10><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 11: k_bfft_fwd<R, B, NT, 11><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 12: k_bfft_fwd<R, B, NT, 12><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 13: k_bfft_fwd<R, B, NT, 13><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 14: k_bfft_fwd<R, B, NT, 14><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 15: k_bfft_fwd<R, B, NT, 15><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 16: k_bfft_fwd<R, B, NT, 16><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    default: return false;
+  }
+}
+template <class R, int B, int NT>
+static bool bfft_inv(int nb, const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
+                     const BoxTw<R> &tw, int final, int n, int lines, const InvOuts<R> &outs, double sc,
+                     cudaStream_t st) {
+  const dim3 grid(B * B * B / NT, lines, n);
+  switch (nb) {
+    case 9: k_bfft_inv<R, B, NT, 9><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 10: k_bfft_inv<R, B, NT, 10><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 11: k_bfft_inv<R, B, NT, 11><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 12: k_bfft_inv<R, B, NT, 12><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 13: k_bfft_inv<R, B, NT, 13><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 14: k_bfft_inv<R, B, NT, 14><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 15: k_bfft_inv<R, B, NT, 15><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 16: k_bfft_inv<R, B, NT, 16><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    default: return false;
+  }
+}
+
 template <class R, int B>
 static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, const int *nin,
                      const InSpec3 *in, const OutSpec<R> *ore, const OutSpec<R> *oim, double scale, cx<R> *Y0,
@@ -191,7 +227,12 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
         case 6: go(k_bdft_fwd<R, B, CHF, NT, REP, 6>, 1); break;
         case 7: go(k_bdft_fwd<R, B, 6, NT, REP, 7>, 1); break;
         case 8: go(k_bdft_fwd<R, B, 7, NT, REP, 8>, 1); break;
-        default: go(k_bdft_fwd<R, B, CHF, NT, REP, 0>, std::max(1, (nb_ax - 1 + CHF - 1) / CHF));
+        default:
+          if constexpr (B == 16) {  // wide boxes: in-register mixed-radix FFTs (box_fft.cuh)
+            if (bfft_fwd<R, B, NT>(nb_ax, in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, n, lines, sp, st))
+              break;
+          }
+          go(k_bdft_fwd<R, B, CHF, NT, REP, 0>, std::max(1, (nb_ax - 1 + CHF - 1) / CHF));
       }
     } else {
       auto go = [&](auto kern, int nch) {
@@ -206,7 +247,13 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
         case 6: go(k_bdft_inv<R, B, CHI, NT, REP, 6>, 1); break;
         case 7: go(k_bdft_inv<R, B, 7, NT, REP, 7>, 1); break;
         case 8: go(k_bdft_inv<R, B, 8, NT, REP, 8>, 1); break;
-        default: go(k_bdft_inv<R, B, CHI, NT, REP, 0>, (nout + CHI - 1) / CHI);
+        default:
+          if constexpr (B == 16) {
+            if (bfft_inv<R, B, NT>(nb_ax, in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, n, lines, outs,
+                                   sc, st))
+              break;
+          }
+          go(k_bdft_inv<R, B, CHI, NT, REP, 0>, (nout + CHI - 1) / CHI);
       }
     }
   };
