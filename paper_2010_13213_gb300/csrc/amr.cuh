@@ -81,6 +81,24 @@ LGF_D R interp_at(int fx, int fy, int fz, F coarse_value) {
   return rnorm(acc);
 }
 
+// The coarse cells the interpolation of a fine block reads: parents (B c)/2 + [0, B/2) per axis and one
+// more on each side, (B/2 + 2)^3 values staged in shared memory (NaN for absent blocks, as fetch gives).
+#define LGF_STAGE_MAX 1000  // (16/2 + 2)^3
+template <class R>
+LGF_D void stage_coarse(R *S, const LevelDev &Lc, const R *buf, int64_t cs, int comp, int4 bc, int B) {
+  const int H = B >> 1, W = H + 2;
+  const int x0 = bc.x * H - 1, y0 = bc.y * H - 1, z0 = bc.z * H - 1;
+  for (int t = threadIdx.x; t < W * W * W; t += blockDim.x)
+    S[t] = fetch<R>(Lc, buf, cs, comp, x0 + t % W, y0 + (t / W) % W, z0 + t / (W * W));
+}
+// P_{k-1->k} at fine cell (x, y, z) of block bc from the staged coarse cube
+template <class R>
+LGF_D R interp_staged(const R *S, int4 bc, int B, int x, int y, int z) {
+  const int H = B >> 1, W = H + 2;
+  const int x0 = bc.x * H - 1, y0 = bc.y * H - 1, z0 = bc.z * H - 1;
+  return interp_at<R>(x, y, z, [&](int i, int j, int k) { return S[((k - z0) * W + (j - y0)) * W + (i - x0)]; });
+}
+
 // ------------------------------------------------------------------ restriction (step 1)
 // grid (nU_k, ncomp), 256 threads.  F_k on the caller blocks of level k (BL index = caller index).
 template <class R>
@@ -126,14 +144,16 @@ __global__ void __launch_bounds__(256) k_coarsen_add(LevelDev Lc, R *Fc, int64_t
 template <class R>
 __global__ void __launch_bounds__(256) k_interp(LevelDev L, const int4 *blocks, R *c, int64_t cs, LevelDev Lc,
                                                 const R *psi, int64_t pcs) {
+  __shared__ R S[LGF_STAGE_MAX];
   const int b = blockIdx.x, comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
+  stage_coarse<R>(S, Lc, psi, pcs, comp, bc, B);
+  __syncthreads();
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
               z = (bc.z << sh) + (off >> (2 * sh));
-    c[comp * cs + (int64_t)b * B3 + off] =
-        interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, psi, pcs, comp, i, j, k); });
+    c[comp * cs + (int64_t)b * B3 + off] = interp_staged<R>(S, bc, B, x, y, z);
   }
 }
 
@@ -159,11 +179,16 @@ __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks,
                                                  const void *f_user, int dtype, int64_t ucs, R *A, int64_t cs,
                                                  const R *c, LevelDev Lc, const R *lpsi, int64_t pcs,
                                                  int has_coarse) {
+  __shared__ R S[LGF_STAGE_MAX];
   const int b = SA[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
   const int u = L.user_of[b];
   const R inv_h2f = RT<R>::from(1.0 / (L.h * L.h));
+  if (has_coarse) {
+    stage_coarse<R>(S, Lc, lpsi, pcs, comp, bc, B);
+    __syncthreads();
+  }
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     const uint8_t cm = L.cellmask[(int64_t)b * B3 + off];
     R v = RT<R>::zero();
@@ -171,7 +196,7 @@ __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks,
     if (has_coarse && (cm & 3)) {
       const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
                 z = (bc.z << sh) + (off >> (2 * sh));
-      const R plp = interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, lpsi, pcs, comp, i, j, k); });
+      const R plp = interp_staged<R>(S, bc, B, x, y, z);
       const R lpc = lap7<R>(L, c, cs, comp, x, y, z, inv_h2f);
       v = v + (plp - lpc);
     }
@@ -292,17 +317,23 @@ template <class R>
 __global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *blocks, const int32_t *HB, const R *F,
                                                     int nU, R *out, int64_t cs, LevelDev Lc, const R *Uc,
                                                     int64_t ucs_c, int has_coarse) {
+  __shared__ R S[LGF_STAGE_MAX];
   const int b = HB[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
+  const bool interp = b >= nU && has_coarse;  // the same for the whole CTA
+  if (interp) {
+    stage_coarse<R>(S, Lc, Uc, ucs_c, comp, bc, B);
+    __syncthreads();
+  }
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     R v = RT<R>::zero();
     if (b < nU) {
       v = F[comp * cs + (int64_t)b * B3 + off];
-    } else if (has_coarse) {
+    } else if (interp) {
       const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
                 z = (bc.z << sh) + (off >> (2 * sh));
-      v = interp_at<R>(x, y, z, [&](int i, int j, int k) { return fetch<R>(Lc, Uc, ucs_c, comp, i, j, k); });
+      v = interp_staged<R>(S, bc, B, x, y, z);
     }
     out[comp * cs + (int64_t)b * B3 + off] = v;
   }
