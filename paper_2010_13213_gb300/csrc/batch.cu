@@ -256,19 +256,40 @@ int lgf_batch_autotune(lgf_batch *b, const void *const *f_dev, void *const *phi_
   double best = 1e300;
   int best_n = b->nstreams;
   int rc = LGF_OK;
+  // each candidate is timed as it will run: a Poisson stage captured into a graph and replayed (eager
+  // stages when cuda_stream cannot capture, e.g. the legacy default stream)
   for (int ns : {4, 8, 16, 32}) {
     if (ns > b->n && ns != 4) continue;
     if ((rc = schedule(b, ns))) break;
+    // one eager stage creates the workspaces of streams not used before (no allocation while capturing)
+    if ((rc = batch_stage(b, f_dev, phi_dev, nullptr, nullptr, st))) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = set_error(LGF_E_CUDA, "autotune stage failed");
+      break;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (st && cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int crc = batch_stage(b, f_dev, phi_dev, nullptr, nullptr, st);
+      cudaGraph_t gr = nullptr;
+      if (cudaStreamEndCapture(st, &gr) == cudaSuccess && gr && !crc) cudaGraphInstantiate(&exec, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+    }
+    cudaGetLastError();
     float ms = 1e30f;
     for (int rep = 0; rep < 3 && !rc; ++rep) {
       cudaEventRecord(e0, st);
-      rc = batch_stage(b, f_dev, phi_dev, nullptr, nullptr, st);
+      if (exec) {
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = set_error(LGF_E_CUDA, "autotune graph launch failed");
+      } else {
+        rc = batch_stage(b, f_dev, phi_dev, nullptr, nullptr, st);
+      }
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(LGF_E_CUDA, "autotune stage failed");
       float m = 0.f;
       cudaEventElapsedTime(&m, e0, e1);
       if (rep) ms = std::min(ms, m);
     }
+    if (exec) cudaGraphExecDestroy(exec);
     if (rc) break;
     if (ms < best) best = ms, best_n = ns;
   }
