@@ -182,23 +182,21 @@ __global__ void __launch_bounds__(NT) k_bfft_fwd(const cx<R> *__restrict__ in, c
     if (ns > 2) add(s2, 2);
     return cx<R>{re, im};
   };
-  // par = 0: even outputs X_{2q} = DFT_NB(x)_q; par = 1: odd outputs X_{2q+1} = DFT_NB(x_j W_P^j)_q.  One
-  // copy of the FFT code serves both (a rolled loop: the unrolled kernel outgrows the instruction cache)
-#pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
-    cx<R> w[NB];
-    if (par == 0) {
+  cx<R> w[NB];
+  // even outputs X_{2q} = DFT_NB(x)_q
 #pragma unroll
-      for (int j = 0; j < NB; ++j) w[j] = fetch(j, false);
-    } else {
+  for (int j = 0; j < NB; ++j) w[j] = fetch(j, false);
+  BFft<R, NB, P, false>::run(w, tw);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) w[j] = bfft_twiddle<R, P, P, false>(fetch(j, true), tw, j);
-    }
-    BFft<R, NB, P, false>::run(w, tw);
+  for (int q = 0; q < NB; ++q)
+    if (!realx || 2 * q <= NB) dst[(2 * q) * bsa] = w[q];
+  // odd outputs X_{2q+1} = DFT_NB(x_j W_P^j)_q
 #pragma unroll
-    for (int q = 0; q < NB; ++q)
-      if (!realx || 2 * q + par <= NB) dst[(2 * q + par) * bsa] = w[q];
-  }
+  for (int j = 0; j < NB; ++j) w[j] = bfft_twiddle<R, P, P, false>(fetch(j, true), tw, j);
+  BFft<R, NB, P, false>::run(w, tw);
+#pragma unroll
+  for (int q = 0; q < NB; ++q)
+    if (!realx || 2 * q + 1 <= NB) dst[(2 * q + 1) * bsa] = w[q];
 }
 
 // Inverse pass for a compile-time block count NB: y_j = sum_{k < P} W_P^{-jk} X_k for the NB box outputs
@@ -257,23 +255,15 @@ __global__ void __launch_bounds__(NT) k_bfft_inv(const cx<R> *__restrict__ in, c
     if (realx && k > NB) return conj(ld_stream(src + (P - k) * bsa));
     return ld_stream(src + k * bsa);
   };
-  cx<R> y[NB];
-  // par = 0: the even inputs' inverse DFT; par = 1: the odd inputs', twiddled by W_P^{-j} and added (one copy
-  // of the FFT code for both)
-#pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
-    cx<R> w[NB];
+  cx<R> y[NB], w[NB];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) w[q] = fetch(2 * q + par);
-    BFft<R, NB, P, true>::run(w, tw);
-    if (par == 0) {
+  for (int q = 0; q < NB; ++q) y[q] = fetch(2 * q);
+  BFft<R, NB, P, true>::run(y, tw);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) y[j] = w[j];
-    } else {
+  for (int q = 0; q < NB; ++q) w[q] = fetch(2 * q + 1);
+  BFft<R, NB, P, true>::run(w, tw);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) y[j] = cnorm(cadd(y[j], bfft_twiddle<R, P, P, true>(w[j], tw, j)));
-    }
-  }
+  for (int j = 0; j < NB; ++j) y[j] = cnorm(cadd(y[j], bfft_twiddle<R, P, P, true>(w[j], tw, j)));
   if (!final) {
     cx<R> *dst = out + field * fstride + lbase + m;
 #pragma unroll
