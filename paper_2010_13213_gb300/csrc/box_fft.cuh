@@ -255,15 +255,24 @@ __global__ void __launch_bounds__(NT) k_bfft_inv(const cx<R> *__restrict__ in, c
     if (realx && k > NB) return conj(ld_stream(src + (P - k) * bsa));
     return ld_stream(src + k * bsa);
   };
-  cx<R> y[NB], w[NB];
+  // the even inputs' inverse DFT waits in shared memory (NB x NT values) while the odd inputs' runs, so
+  // only one line of values is held in registers at a time
+  extern __shared__ __align__(16) unsigned char bfft_smem[];
+  cx<R> *SE = reinterpret_cast<cx<R> *>(bfft_smem);
+  {
+    cx<R> w[NB];
 #pragma unroll
-  for (int q = 0; q < NB; ++q) y[q] = fetch(2 * q);
+    for (int q = 0; q < NB; ++q) w[q] = fetch(2 * q);
+    BFft<R, NB, P, true>::run(w, tw);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) SE[j * NT + threadIdx.x] = w[j];
+  }
+  cx<R> y[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) y[q] = fetch(2 * q + 1);
   BFft<R, NB, P, true>::run(y, tw);
 #pragma unroll
-  for (int q = 0; q < NB; ++q) w[q] = fetch(2 * q + 1);
-  BFft<R, NB, P, true>::run(w, tw);
-#pragma unroll
-  for (int j = 0; j < NB; ++j) y[j] = cnorm(cadd(y[j], bfft_twiddle<R, P, P, true>(w[j], tw, j)));
+  for (int j = 0; j < NB; ++j) y[j] = cnorm(cadd(SE[j * NT + threadIdx.x], bfft_twiddle<R, P, P, true>(y[j], tw, j)));
   if (!final) {
     cx<R> *dst = out + field * fstride + lbase + m;
 #pragma unroll

@@ -145,14 +145,14 @@ static bool bfft_inv(int nb, const cx<R> *in, cx<R> *out, int64_t fstride, const
                      cudaStream_t st) {
   const dim3 grid(B * B * B / NT, lines, n);
   switch (nb) {
-    case 9: k_bfft_inv<R, B, NT, 9><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 10: k_bfft_inv<R, B, NT, 10><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 11: k_bfft_inv<R, B, NT, 11><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 12: k_bfft_inv<R, B, NT, 12><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 13: k_bfft_inv<R, B, NT, 13><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 14: k_bfft_inv<R, B, NT, 14><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 15: k_bfft_inv<R, B, NT, 15><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
-    case 16: k_bfft_inv<R, B, NT, 16><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 9: k_bfft_inv<R, B, NT, 9><<<grid, NT, 9 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 10: k_bfft_inv<R, B, NT, 10><<<grid, NT, 10 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 11: k_bfft_inv<R, B, NT, 11><<<grid, NT, 11 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 12: k_bfft_inv<R, B, NT, 12><<<grid, NT, 12 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 13: k_bfft_inv<R, B, NT, 13><<<grid, NT, 13 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 14: k_bfft_inv<R, B, NT, 14><<<grid, NT, 14 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 15: k_bfft_inv<R, B, NT, 15><<<grid, NT, 15 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 16: k_bfft_inv<R, B, NT, 16><<<grid, NT, 16 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
     default: return false;
   }
 }
