@@ -128,6 +128,11 @@ static bool bfft_fwd(int nb, const cx<R> *in, cx<R> *out, int64_t fstride, const
                      const BoxTw<R> &tw, int gather, int n, int lines, const FwdSpecs &sp, cudaStream_t st) {
   const dim3 grid(B * B * B / NT, lines, n);
   switch (nb) {
+    case 4: k_bfft_fwd<R, B, NT, 4><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 5: k_bfft_fwd<R, B, NT, 5><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 6: k_bfft_fwd<R, B, NT, 6><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 7: k_bfft_fwd<R, B, NT, 7><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 8: k_bfft_fwd<R, B, NT, 8><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
     case 9: k_bfft_fwd<R, B, NT, 9><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
     case 10: k_bfft_fwd<R, B, NT, 10><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
     case 11: k_bfft_fwd<R, B, NT, 11><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
@@ -145,6 +150,11 @@ static bool bfft_inv(int nb, const cx<R> *in, cx<R> *out, int64_t fstride, const
                      cudaStream_t st) {
   const dim3 grid(B * B * B / NT, lines, n);
   switch (nb) {
+    case 4: k_bfft_inv<R, B, NT, 4><<<grid, NT, 4 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 5: k_bfft_inv<R, B, NT, 5><<<grid, NT, 5 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 6: k_bfft_inv<R, B, NT, 6><<<grid, NT, 6 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 7: k_bfft_inv<R, B, NT, 7><<<grid, NT, 7 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
+    case 8: k_bfft_inv<R, B, NT, 8><<<grid, NT, 8 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
     case 9: k_bfft_inv<R, B, NT, 9><<<grid, NT, 9 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
     case 10: k_bfft_inv<R, B, NT, 10><<<grid, NT, 10 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
     case 11: k_bfft_inv<R, B, NT, 11><<<grid, NT, 11 * NT * sizeof(cx<R>), st>>>(in, out, fstride, g, ax, ext, tw, final, outs, sc); return true;
@@ -219,6 +229,11 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
         kern<<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax),
                                                                    gather, nch, sp);
       };
+      if constexpr (B == 16) {  // 4..16 blocks: in-register mixed-radix FFTs (box_fft.cuh)
+        if (nb_ax >= 4 && bfft_fwd<R, B, NT>(nb_ax, in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), gather, n, lines,
+                                             sp, st))
+          return;
+      }
       switch (nb_ax) {
         case 2: go(k_bdft_fwd<R, B, CHF, NT, REP, 2>, 1); break;
         case 3: go(k_bdft_fwd<R, B, CHF, NT, REP, 3>, 1); break;
@@ -239,6 +254,11 @@ static int box_group(const BoxSpec *S, const std::vector<int> &fields, int nc, c
         kern<<<dim3(B3 / (NT * REP), lines, n * nch), NT, 0, st>>>(in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax),
                                                                    final, nch, outs, sc);
       };
+      if constexpr (B == 16) {
+        if (nb_ax >= 4 && bfft_inv<R, B, NT>(nb_ax, in_, out_, fstride, g, ax, ext, btw_of<R>(S, ax), final, n, lines,
+                                             outs, sc, st))
+          return;
+      }
       switch (nb_ax) {
         case 2: go(k_bdft_inv<R, B, CHI, NT, REP, 2>, 1); break;
         case 3: go(k_bdft_inv<R, B, CHI, NT, REP, 3>, 1); break;
