@@ -10,6 +10,8 @@
 // Fields are stored per level as [ncomp][nBL][B^3] over the level's internal block set; a dense
 // block map (block coords -> index, -1 if absent) gives neighbours across block boundaries.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 struct LevelDev {
@@ -322,6 +324,8 @@ static __global__ void __launch_bounds__(256)
 struct HeatW {
   double w[65];  // w[n] = e^{-2 alpha} I_n(2 alpha), n <= r
   int r;
+  int rd;        // taps n <= rd carry the double-float arithmetic; taps beyond have w[n] < 2^-30, so their
+                 // products in FP32 (relative error 2^-24) err by less than 2^-54 of the values they read
 };
 
 // P_k fhat, the level-k reconstruction of the AMR data (Sec. 3.2, Eq. (eq:interp)); grid (|HB_k|, ncomp).
@@ -411,11 +415,28 @@ __global__ void __launch_bounds__(B * B) k_heat_line(LevelDev L, const int4 *blo
   const R w0 = wt[0];
 #pragma unroll
   for (int la = 0; la < B; ++la) acc[la] = w0 * S[(la + r) * QS + q];
-  for (int d = 1; d <= r; ++d) {
+  constexpr bool DF = std::is_same<R, df>::value;
+  const int rd = DF ? min(w.rd, r) : r;
+  for (int d = 1; d <= rd; ++d) {
     const R wd = wt[d];
     const R *Sp = S + (r + d) * QS + q, *Sm = S + (r - d) * QS + q;
 #pragma unroll
     for (int la = 0; la < B; ++la) acc[la] = rfma(acc[la], wd, radd(Sp[la * QS], Sm[la * QS]));
+  }
+  if constexpr (DF) {  // the far taps in FP32 on the high words
+    if (rd < r) {
+      float facc[B];
+#pragma unroll
+      for (int la = 0; la < B; ++la) facc[la] = 0.0f;
+      for (int d = rd + 1; d <= r; ++d) {
+        const float wd = wt[d].hi;
+        const R *Sp = S + (r + d) * QS + q, *Sm = S + (r - d) * QS + q;
+#pragma unroll
+        for (int la = 0; la < B; ++la) facc[la] = fmaf(wd, Sp[la * QS].hi + Sm[la * QS].hi, facc[la]);
+      }
+#pragma unroll
+      for (int la = 0; la < B; ++la) acc[la] = radd(acc[la], df{facc[la], 0.0f});
+    }
   }
   __syncthreads();  // every read of the tile is done before it is overwritten
 #pragma unroll

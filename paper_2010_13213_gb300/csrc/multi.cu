@@ -504,7 +504,11 @@ static int heat_weights(double alpha, HeatW *w) {
   if (r < 0) r = 0;
   if (r > 64) return set_error(LGF_E_UNSUPPORTED, "heat kernel radius %d above 64 (alpha %.3g too large)", r, alpha);
   w->r = r;
-  for (int n = 0; n <= 64; ++n) w->w[n] = n <= r ? tmp[n] : 0.0;
+  w->rd = 0;
+  for (int n = 0; n <= 64; ++n) {
+    w->w[n] = n <= r ? tmp[n] : 0.0;
+    if (n <= r && tmp[n] >= 0x1p-30) w->rd = n;
+  }
   return LGF_OK;
 }
 
