@@ -63,22 +63,6 @@ LGF_D R lap7(const LevelDev &L, const R *buf, int64_t cs, int comp, int x, int y
   return (s - RT<R>::from(6.0) * c) * inv_h2;
 }
 
-// The same for the cell at offset `off` of block `blk`: cells inside the block read their neighbours
-// directly (no block-map lookups), cells on the block's surface go through the map.
-template <class R>
-LGF_D R lap7_in(const LevelDev &L, const R *buf, int64_t cs, int comp, int blk, int off, int x, int y, int z,
-                R inv_h2) {
-  const int B = 1 << L.shift, m = B - 1;
-  const int lx = off & m, ly = (off >> L.shift) & m, lz = off >> (2 * L.shift);
-  if (lx == 0 || ly == 0 || lz == 0 || lx == m || ly == m || lz == m) return lap7<R>(L, buf, cs, comp, x, y, z, inv_h2);
-  const R *p = buf + comp * cs + ((int64_t)blk << (3 * L.shift)) + off;
-  const int sy = B, sz = B * B;
-  R s = p[1] + p[-1];
-  s = s + p[sy] + p[-sy];
-  s = s + p[sz] + p[-sz];
-  return (s - RT<R>::from(6.0) * p[0]) * inv_h2;
-}
-
 // P_{k-1->k}: fine cell (fx, fy, fz) -> sum over the 8 coarse corners of prod (3/4 | 1/4) * value.  The
 // weights are 27, 9, 3 or 1 / 64 (exact floats); products and sums run lazily in double-float, with one
 // renormalisation at the end.
@@ -186,7 +170,7 @@ __global__ void __launch_bounds__(256) k_lap(LevelDev L, const int4 *blocks, con
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
               z = (bc.z << sh) + (off >> (2 * sh));
-    out[comp * cs + (int64_t)b * B3 + off] = lap7_in<R>(L, psi, cs, comp, b, off, x, y, z, inv_h2);
+    out[comp * cs + (int64_t)b * B3 + off] = lap7<R>(L, psi, cs, comp, x, y, z, inv_h2);
   }
 }
 
@@ -215,7 +199,7 @@ __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks,
       const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
                 z = (bc.z << sh) + (off >> (2 * sh));
       const R plp = interp_staged<R>(S, bc, B, x, y, z);
-      const R lpc = lap7_in<R>(L, c, cs, comp, b, off, x, y, z, inv_h2f);
+      const R lpc = lap7<R>(L, c, cs, comp, x, y, z, inv_h2f);
       v = v + (plp - lpc);
     }
     A[comp * cs + (int64_t)b * B3 + off] = v;
