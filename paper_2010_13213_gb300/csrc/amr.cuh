@@ -10,8 +10,6 @@
 // Fields are stored per level as [ncomp][nBL][B^3] over the level's internal block set; a dense
 // block map (block coords -> index, -1 if absent) gives neighbours across block boundaries.
 #pragma once
-#include <type_traits>
-
 #include "common.cuh"
 
 struct LevelDev {
@@ -62,6 +60,41 @@ LGF_D R lap7(const LevelDev &L, const R *buf, int64_t cs, int comp, int x, int y
   s = s + fetch<R>(L, buf, cs, comp, x, y, z + 1) + fetch<R>(L, buf, cs, comp, x, y, z - 1);
   return (s - RT<R>::from(6.0) * c) * inv_h2;
 }
+
+// The values of an internal field on block b and on the one-cell face halo around it, staged in shared
+// memory as a (B + 2)^3 cube S[((z + 1) W + y + 1) W + x + 1] (W = B + 2, local x, y, z in [-1, B]; edges and
+// corners are not written).  Halo cells of absent blocks are NaN, as fetch gives.
+template <class R>
+LGF_D void stage_block_halo(R *S, const LevelDev &L, const R *buf, int64_t cs, int comp, int b, int4 bc) {
+  const int sh = L.shift, B = 1 << sh, W = B + 2, B2 = B * B, B3 = B2 * B;
+  const R *src = buf + comp * cs;
+  for (int t = threadIdx.x; t < B3; t += blockDim.x) {
+    const int x = t & (B - 1), y = (t >> sh) & (B - 1), z = t >> (2 * sh);
+    S[((z + 1) * W + y + 1) * W + x + 1] = src[((int64_t)b << (3 * sh)) + t];
+  }
+  for (int t = threadIdx.x; t < 6 * B2; t += blockDim.x) {
+    const int f = t >> (2 * sh), a = f >> 1, hi = f & 1, u = t & (B - 1), v = (t >> sh) & (B - 1);
+    const int e = hi ? B : -1;  // the face's coordinate along axis a
+    const int x = a == 0 ? e : u, y = a == 1 ? e : (a == 0 ? u : v), z = a == 2 ? e : v;
+    const int nb = level_block(L, bc.x + (a == 0 ? (hi ? 1 : -1) : 0), bc.y + (a == 1 ? (hi ? 1 : -1) : 0),
+                               bc.z + (a == 2 ? (hi ? 1 : -1) : 0));
+    R val = nan_of<R>();
+    if (nb >= 0)
+      val = src[((int64_t)nb << (3 * sh)) + ((((z & (B - 1)) << sh) + (y & (B - 1))) << sh) + (x & (B - 1))];
+    S[((z + 1) * W + y + 1) * W + x + 1] = val;
+  }
+}
+// 7-point Laplacian at local cell (x, y, z) of a staged cube (the same sums in the same order as lap7)
+template <class R>
+LGF_D R lap7_staged(const R *S, int W, int x, int y, int z, R inv_h2) {
+  const int i = ((z + 1) * W + y + 1) * W + x + 1, W2 = W * W;
+  R s = S[i + 1] + S[i - 1];
+  s = s + S[i + W] + S[i - W];
+  s = s + S[i + W2] + S[i - W2];
+  return (s - RT<R>::from(6.0) * S[i]) * inv_h2;
+}
+template <class R>
+LGF_HD constexpr size_t halo_smem(int B) { return sizeof(R) * (size_t)(B + 2) * (B + 2) * (B + 2); }
 
 // P_{k-1->k}: fine cell (fx, fy, fz) -> sum over the 8 coarse corners of prod (3/4 | 1/4) * value.  The
 // weights are 27, 9, 3 or 1 / 64 (exact floats); products and sums run lazily in double-float, with one
@@ -160,28 +193,35 @@ __global__ void __launch_bounds__(256) k_interp(LevelDev L, const int4 *blocks, 
 }
 
 // ------------------------------------------------------------------ coarse Laplacian L_{k-1} psi_{k-1}
-// Every cell of the coarse level's blocks (NaN next to an absent block, as fetch gives); grid (nBL, ncomp).
+// Every cell of the listed blocks of the coarse level (NaN next to an absent block, as fetch gives); grid
+// (|list|, ncomp), 512 threads, halo_smem<R>(B) bytes of dynamic shared memory (the block and its face halo;
+// 512 threads keep 2048 resident per SM at four CTAs).
 template <class R>
-__global__ void __launch_bounds__(256) k_lap(LevelDev L, const int4 *blocks, const R *psi, R *out, int64_t cs) {
-  const int b = blockIdx.x, comp = blockIdx.y, sh = L.shift, B = 1 << sh;
+__global__ void __launch_bounds__(512) k_lap(LevelDev L, const int4 *blocks, const int32_t *list, const R *psi,
+                                             R *out, int64_t cs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *S = reinterpret_cast<R *>(smem_raw);
+  const int b = list[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
-  const int4 bc = blocks[b];
   const R inv_h2 = RT<R>::from(1.0 / (L.h * L.h));
-  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
-    const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
-              z = (bc.z << sh) + (off >> (2 * sh));
-    out[comp * cs + (int64_t)b * B3 + off] = lap7<R>(L, psi, cs, comp, x, y, z, inv_h2);
-  }
+  stage_block_halo<R>(S, L, psi, cs, comp, b, blocks[b]);
+  __syncthreads();
+  for (int off = threadIdx.x; off < B3; off += blockDim.x)
+    out[comp * cs + (int64_t)b * B3 + off] =
+        lap7_staged<R>(S, B + 2, off & (B - 1), (off >> sh) & (B - 1), off >> (2 * sh), inv_h2);
 }
 
 // ------------------------------------------------------------------ correction source A_k
-// grid (|SA_k|, ncomp).  A[b] for b = SA[i].  k = 0: A = [OM] fhat.  `lpsi` = L_{k-1} psi_{k-1} (k_lap).
+// grid (|SA_k|, ncomp), 512 threads.  A[b] for b = SA[i].  k = 0: A = [OM] fhat.  `lpsi` = L_{k-1} psi_{k-1}
+// (k_lap).  With has_coarse: halo_smem<R>(B) bytes of dynamic shared memory (c on the block and its face halo).
 template <class R>
-__global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks, const int32_t *SA,
+__global__ void __launch_bounds__(512) k_correct(LevelDev L, const int4 *blocks, const int32_t *SA,
                                                  const void *f_user, int dtype, int64_t ucs, R *A, int64_t cs,
                                                  const R *c, LevelDev Lc, const R *lpsi, int64_t pcs,
                                                  int has_coarse) {
   __shared__ R S[LGF_STAGE_MAX];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *C = reinterpret_cast<R *>(smem_raw);
   const int b = SA[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
   const int B3 = B * B * B;
   const int4 bc = blocks[b];
@@ -189,6 +229,7 @@ __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks,
   const R inv_h2f = RT<R>::from(1.0 / (L.h * L.h));
   if (has_coarse) {
     stage_coarse<R>(S, Lc, lpsi, pcs, comp, bc, B);
+    stage_block_halo<R>(C, L, c, cs, comp, b, bc);
     __syncthreads();
   }
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
@@ -196,10 +237,9 @@ __global__ void __launch_bounds__(256) k_correct(LevelDev L, const int4 *blocks,
     R v = RT<R>::zero();
     if ((cm & 1) && u >= 0) v = load_field<R>(f_user, comp * ucs + (int64_t)u * B3 + off, dtype);
     if (has_coarse && (cm & 3)) {
-      const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
-                z = (bc.z << sh) + (off >> (2 * sh));
-      const R plp = interp_staged<R>(S, bc, B, x, y, z);
-      const R lpc = lap7<R>(L, c, cs, comp, x, y, z, inv_h2f);
+      const int lx = off & (B - 1), ly = (off >> sh) & (B - 1), lz = off >> (2 * sh);
+      const R plp = interp_staged<R>(S, bc, B, (bc.x << sh) + lx, (bc.y << sh) + ly, (bc.z << sh) + lz);
+      const R lpc = lap7_staged<R>(C, B + 2, lx, ly, lz, inv_h2f);
       v = v + (plp - lpc);
     }
     A[comp * cs + (int64_t)b * B3 + off] = v;
@@ -308,8 +348,6 @@ static __global__ void __launch_bounds__(256)
 struct HeatW {
   double w[65];  // w[n] = e^{-2 alpha} I_n(2 alpha), n <= r
   int r;
-  int rd;        // taps n <= rd carry the double-float arithmetic; taps beyond have w[n] < 2^-30, so their
-                 // products in FP32 (relative error 2^-24) err by less than 2^-54 of the values they read
 };
 
 // P_k fhat, the level-k reconstruction of the AMR data (Sec. 3.2, Eq. (eq:interp)); grid (|HB_k|, ncomp).
@@ -399,28 +437,11 @@ __global__ void __launch_bounds__(B * B) k_heat_line(LevelDev L, const int4 *blo
   const R w0 = wt[0];
 #pragma unroll
   for (int la = 0; la < B; ++la) acc[la] = w0 * S[(la + r) * QS + q];
-  constexpr bool DF = std::is_same<R, df>::value;
-  const int rd = DF ? min(w.rd, r) : r;
-  for (int d = 1; d <= rd; ++d) {
+  for (int d = 1; d <= r; ++d) {
     const R wd = wt[d];
     const R *Sp = S + (r + d) * QS + q, *Sm = S + (r - d) * QS + q;
 #pragma unroll
     for (int la = 0; la < B; ++la) acc[la] = rfma(acc[la], wd, radd(Sp[la * QS], Sm[la * QS]));
-  }
-  if constexpr (DF) {  // the far taps in FP32 on the high words
-    if (rd < r) {
-      float facc[B];
-#pragma unroll
-      for (int la = 0; la < B; ++la) facc[la] = 0.0f;
-      for (int d = rd + 1; d <= r; ++d) {
-        const float wd = wt[d].hi;
-        const R *Sp = S + (r + d) * QS + q, *Sm = S + (r - d) * QS + q;
-#pragma unroll
-        for (int la = 0; la < B; ++la) facc[la] = fmaf(wd, Sp[la * QS].hi + Sm[la * QS].hi, facc[la]);
-      }
-#pragma unroll
-      for (int la = 0; la < B; ++la) acc[la] = radd(acc[la], df{facc[la], 0.0f});
-    }
   }
   __syncthreads();  // every read of the tile is done before it is overwritten
 #pragma unroll

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <list>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,17 @@ namespace lgf {
 
 double box_cost(int B, const int nb[3]);
 double pair_cost(int B, double nsrc, double ntgt);
+
+// Dynamic shared memory of k_correct with the correction (the staged c cube; with the static coarse cube
+// above the default 48 KB for 8-byte arithmetics, so the limit is raised once per arithmetic).
+template <class R>
+static size_t correct_smem(int B) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_correct<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)halo_smem<R>(16));
+  });
+  return halo_smem<R>(B);
+}
 
 // ------------------------------------------------------------------ plan cache (process-wide)
 static std::mutex g_plan_mu;
@@ -241,13 +253,13 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     }
     const bool corr = k > 0 && !(o.flags & LGF_SOLVE_NO_CORRECTION);
     if (nSA) {
-      if (corr) {  // L_{k-1} psi_{k-1} once per coarse cell, then interpolated per fine cell
-        k_lap<R><<<dim3((unsigned)P->L[k - 1].BL.size(), ncomp), 256, 0, st>>>(Lc, P->L[k - 1].d_BL, psi_prev, Lpsi,
-                                                                               ccs);
+      if (corr && !L.LP.empty()) {  // L_{k-1} psi_{k-1} once per coarse cell read, then interpolated per fine cell
+        k_lap<R><<<dim3((unsigned)L.LP.size(), ncomp), 512, halo_smem<R>(B), st>>>(
+            Lc, P->L[k - 1].d_BL, lists + L.off_LP, psi_prev, Lpsi, ccs);
         LGF_LAUNCH_CHECK("coarse Laplacian");
       }
-      k_correct<R><<<dim3(nSA, ncomp), 256, 0, st>>>(Ld, L.d_BL, lists + L.off_SA, f, dtype, ucs, A, cs[k], c, Lc,
-                                                     Lpsi, ccs, corr);
+      k_correct<R><<<dim3(nSA, ncomp), 512, corr ? correct_smem<R>(B) : 0, st>>>(
+          Ld, L.d_BL, lists + L.off_SA, f, dtype, ucs, A, cs[k], c, Lc, Lpsi, ccs, corr);
       LGF_LAUNCH_CHECK("correct");
       tm.mark(PH_CORRECT);
     }
@@ -504,11 +516,7 @@ static int heat_weights(double alpha, HeatW *w) {
   if (r < 0) r = 0;
   if (r > 64) return set_error(LGF_E_UNSUPPORTED, "heat kernel radius %d above 64 (alpha %.3g too large)", r, alpha);
   w->r = r;
-  w->rd = 0;
-  for (int n = 0; n <= 64; ++n) {
-    w->w[n] = n <= r ? tmp[n] : 0.0;
-    if (n <= r && tmp[n] >= 0x1p-30) w->rd = n;
-  }
+  for (int n = 0; n <= 64; ++n) w->w[n] = n <= r ? tmp[n] : 0.0;
   return LGF_OK;
 }
 

@@ -339,6 +339,32 @@ int build_plan(const lgf_mesh *m, const int *heat_radii, Plan **out) {
     lists.insert(lists.end(), L.Tpsi.begin(), L.Tpsi.end());
     L.off_HB = (int)lists.size();
     lists.insert(lists.end(), L.HB.begin(), L.HB.end());
+    // LP: the coarse blocks under the SA blocks' interpolation stencils (parent cells and one more on each
+    // side: coarse cells B c / 2 - 1 .. B c / 2 + B / 2 per axis), as they exist on level k - 1
+    L.LP.clear();
+    if (k >= 1) {
+      const LevelPlan &Lc = P->L[k - 1];
+      std::vector<char> need(Lc.BL.size(), 0);
+      auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+      const int H = B / 2;
+      for (int b : L.SA) {
+        const int v[3] = {L.BL[b].x, L.BL[b].y, L.BL[b].z};
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) lo[a] = fdiv(v[a] * H - 1, B), hi[a] = fdiv(v[a] * H + H, B);
+        for (int z = lo[2]; z <= hi[2]; ++z)
+          for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+              const int bx = x - Lc.bb_lo[0], by = y - Lc.bb_lo[1], bz = z - Lc.bb_lo[2];
+              if (bx < 0 || by < 0 || bz < 0 || bx >= Lc.bb_n[0] || by >= Lc.bb_n[1] || bz >= Lc.bb_n[2]) continue;
+              const int i = Lc.map[((size_t)bz * Lc.bb_n[1] + by) * Lc.bb_n[0] + bx];
+              if (i >= 0) need[i] = 1;
+            }
+      }
+      for (int i = 0; i < (int)need.size(); ++i)
+        if (need[i]) L.LP.push_back(i);
+    }
+    L.off_LP = (int)lists.size();
+    lists.insert(lists.end(), L.LP.begin(), L.LP.end());
     // block-index FFT box
     {
       int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};

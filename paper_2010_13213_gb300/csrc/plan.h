@@ -34,19 +34,21 @@ struct LevelPlan {
   std::vector<uint8_t> octcov;     // [nBL] covered octants (bit o = octant (x>=B/2)+2(y>=B/2)+4(z>=B/2))
   std::vector<int32_t> SA, SB, Tphi, Tpsi;  // lists of BL indices (Poisson)
   std::vector<int32_t> HB;         // heat block set (BL indices)
+  std::vector<int32_t> LP;         // k >= 1: level-(k-1) BL indices whose L_{k-1} psi_{k-1} the correction of
+                                   // the SA blocks reads (the coarse cubes k_correct stages)
   std::vector<uint8_t> phi_oct;    // [|Tphi|] octants of Omega_k (write mask)
   // device copies
   int32_t *d_map = nullptr;
   int4 *d_BL = nullptr;
   uint8_t *d_cellmask = nullptr;
   uint8_t *d_octcov = nullptr;
-  int32_t *d_lists = nullptr;      // SA | SB | Tall(=Tphi then Tpsi\Tphi) | psi rows | Tpsi | HB
+  int32_t *d_lists = nullptr;      // SA | SB | Tall(=Tphi then Tpsi\Tphi) | psi rows | Tpsi | HB | LP
   uint8_t *d_phi_oct = nullptr;
   int32_t *d_user_of = nullptr;    // [nBL] global caller block index or -1
   std::vector<int32_t> Tall;       // Tphi then Tpsi minus Tphi
   std::vector<int32_t> psi_rows;   // rows of Tall that are psi targets
   int nTall = 0;
-  int off_SA = 0, off_SB = 0, off_Tall = 0, off_psi = 0, off_Tpsi = 0, off_HB = 0;
+  int off_SA = 0, off_SB = 0, off_Tall = 0, off_psi = 0, off_Tpsi = 0, off_HB = 0, off_LP = 0;
   int heat_r = 0;                  // heat kernel radius at this level
   int64_t n_omega = 0;             // |Omega_k| in cells
   int64_t n_src = 0;               // cells carrying a source of the level's convolutions (OM, EX or COV)
