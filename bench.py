@@ -285,19 +285,28 @@ def batch_poisson(L, torch, dev, steps, warmup, world, pk, fp64=True, check=True
             torch.cuda.synchronize()
             res[name]["phis"] = [p.cpu().numpy() for p in phis]
         if name == "df32":
-            # end to end through the C ABI: every step copies all sources in from pinned host memory,
-            # replays the graph and copies all results out (one stream)
+            # end to end through the C ABI with host buffers: (a) the serial form, every step copies all
+            # sources in from pinned host memory on one stream, replays the graph, copies all results out;
+            # (b) lgf_batch_graph_create_io, the same copies inside the graph on the instances' streams
             hin = [h.pin_memory() for h in host]
             hout = [torch.empty_like(h).pin_memory() for h in host]
 
             def e2e_step():
-                for d, h in zip(fs, hin):
-                    d.copy_(h, non_blocking=True)
-                b.graph_launch(bs.cuda_stream)
-                for h, d in zip(hout, phis):
-                    h.copy_(d, non_blocking=True)
+                with torch.cuda.stream(bs):
+                    for d, h in zip(fs, hin):
+                        d.copy_(h, non_blocking=True)
+                    b.graph_launch(bs.cuda_stream)
+                    for h, d in zip(hout, phis):
+                        h.copy_(d, non_blocking=True)
 
-            res["e2e_ms"] = time_calls(torch, e2e_step, max(3, steps // 2), 2, bs, world=world)
+            res["e2e_serial_ms"] = time_calls(torch, e2e_step, max(3, steps // 2), 2, bs, world=world)
+            b.graph_create_io(ptr(hin), ptr(hout), ptr(fs), ptr(phis), bs.cuda_stream)
+            res["e2e_ms"] = time_calls(torch, lambda: b.graph_launch(bs.cuda_stream), max(3, steps // 2), 2, bs,
+                                       world=world)
+            res["e2e_nodes"] = b.graph_nodes()
+            if check:
+                torch.cuda.synchronize()
+                res["e2e_match"] = all(torch.equal(h, d.cpu()) for h, d in zip(hout, phis))
             res["e2e_bytes"] = int(sum(h.numel() * 8 for h in host))
         b.close()
     # per-kernel time: the same solves one by one with the library's phase events (CUDA events on the
@@ -709,8 +718,8 @@ def run_gpu(args):
         hb = batch_poisson(L, torch, dev, args.steps, args.warmup, world, pk)
     clocks = clk.summary()
     res = hb["res"]
-    mx = max_over_ranks([res["df32"]["ms"], res["fp64"]["ms"], res["e2e_ms"]], world, dev)
-    ms_df, ms_64, ms_e2e = mx
+    mx = max_over_ranks([res["df32"]["ms"], res["fp64"]["ms"], res["e2e_ms"], res["e2e_serial_ms"]], world, dev)
+    ms_df, ms_64, ms_e2e, ms_e2e_serial = mx
     # accuracy of a seeded sample of instances against the oracle, and the oracle's own time on it (the
     # CPU baseline), both outside the timed region
     sample = batch_sample(hb["params"], hb["cells"])
@@ -780,8 +789,12 @@ def run_gpu(args):
                              "threads_used": _oracle_threads()},
             "e2e": {"value": replica_rate(total, ms_e2e, world), "unit": "Mcells/s",
                     "h2d_bytes_per_step": res["e2e_bytes"], "d2h_bytes_per_step": res["e2e_bytes"],
-                    "note": "one stream: all 64 sources copied in from pinned host memory, the graph replayed, all "
-                            "64 results copied out, every step"},
+                    "note": "every step: all 64 sources copied in from pinned host memory and all 64 results "
+                            "copied out inside one graph (lgf_batch_graph_create_io: each instance's copies on the "
+                            "stream that solves it, overlapping the other instances' solves)",
+                    "graph_nodes": res["e2e_nodes"], "results_match_device_graph": res.get("e2e_match"),
+                    "serial": {"value": replica_rate(total, ms_e2e_serial, world), "unit": "Mcells/s",
+                               "note": "one stream: all copies in, the device graph, all copies out"}},
             "gpu_launches": int(hb["launches"]) * args.steps,
             "table_build_s": hb["t_table"],
             "clocks": clocks,

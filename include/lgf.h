@@ -346,13 +346,28 @@ int lgf_batch_graph_create(lgf_batch *b, int32_t nstages, const void *const *f_d
 int lgf_batch_graph_launch(lgf_batch *b, void *cuda_stream);
 
 /*
+ * lgf_batch_graph_create_io -- capture one Poisson stage (phi = L^{-1} f per instance, Sec. 3.4) with its
+ * host transfers inside the graph: per instance, on the stream that solves it, f_host[i] -> f_dev[i] before
+ * the solve and phi_dev[i] -> phi_host[i] after it, so one instance's copies overlap the others' solves.
+ *   f_host, phi_host : host [ninst] pointers to PINNED host buffers (cudaHostAlloc or cudaHostRegister),
+ *                      each the instance's field bytes (ncomp x its blocks x B^3 x 8 or 4 for the dtype);
+ *                      pageable memory is rejected with LGF_E_INVALID_ARG.  Owned by the caller.
+ *   f_dev, phi_dev   : host [ninst] device buffers of the same sizes (the staging copies).
+ * Runs the stage once eagerly (copies included), then captures; synchronises.  lgf_batch_graph_launch
+ * replays it; phi_host holds the results once cuda_stream reaches the end of the replay.
+ */
+int lgf_batch_graph_create_io(lgf_batch *b, const void *const *f_host, void *const *phi_host,
+                              const void *const *f_dev, void *const *phi_dev, void *cuda_stream);
+
+/*
  * lgf_batch_autotune -- measure and choose how the batch runs (the batched solver's autotuner):
  *   (i)  per instance, the evaluation of its block-index DFT passes: the CUDA-core conjugate-pair passes or,
  *        for DF32 / FP32 solves, the tensor-core DFT-GEMM with 5 / 3 digit slices (the fewest that keep the
  *        arithmetic's accuracy), whichever solves the instance faster (three timed solves each);
  *   (ii) the instance order, longest measured solve first, dealt to the least-loaded stream;
  *   (iii) the stream count from {4, 8, 16, 32}, by timing a Poisson stage captured into a graph and
- *        replayed (eager stages when cuda_stream cannot capture, e.g. the legacy default stream).
+ *        replayed (the fastest of five replays; eager stages when cuda_stream cannot capture, e.g. the
+ *        legacy default stream); a larger count is taken only when it is at least 1 % faster.
  * f_dev / phi_dev: the instances' fields (phi is overwritten).  Synchronises cuda_stream.  A graph captured
  * before the call keeps the old choices; capture after it.
  */

@@ -103,6 +103,7 @@ def load():
         lib.lgf_batch_stage.argtypes = [c_void_p, PP, PP, PP, POINTER(c_double), c_void_p]
         lib.lgf_batch_graph_create.argtypes = [c_void_p, c_int32, PP, PP, PP, PP, POINTER(c_double), c_void_p]
         lib.lgf_batch_graph_launch.argtypes = [c_void_p, c_void_p]
+        lib.lgf_batch_graph_create_io.argtypes = [c_void_p, PP, PP, PP, PP, c_void_p]
         lib.lgf_batch_graph_nodes.argtypes = [c_void_p, POINTER(c_int64)]
         lib.lgf_batch_autotune.argtypes = [c_void_p, PP, PP, c_void_p]
         lib.lgf_batch_tuning.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_double)]
@@ -115,6 +116,7 @@ def load():
                      "lgf_refinement_indicator", "lgf_stage_projection", "lgf_table_prepare", "lgf_batch_create",
                      "lgf_batch_destroy",
                      "lgf_batch_stage", "lgf_batch_graph_create", "lgf_batch_graph_launch", "lgf_batch_graph_nodes",
+                     "lgf_batch_graph_create_io",
                      "lgf_batch_autotune", "lgf_batch_tuning",
                      "lgf_device_status", "lgf_selftest_wait_timeout"):
             getattr(lib, name).restype = c_int32
@@ -294,6 +296,14 @@ class Batch:
             flat = [float(a) for row in alpha_stages for a in row]
             al = (c_double * len(flat))(*flat)
         _check(load().lgf_batch_graph_create(c_void_p(self.h), int(nstages), f, p, g, t, al, c_void_p(cuda_stream)))
+
+    def graph_create_io(self, f_host_ptrs, phi_host_ptrs, f_ptrs, phi_ptrs, cuda_stream: int):
+        """One Poisson stage with the pinned host transfers inside the graph."""
+        fh, _a = _ptrs(f_host_ptrs)
+        ph, _b = _ptrs(phi_host_ptrs)
+        f, _c = _ptrs(f_ptrs)
+        p, _d = _ptrs(phi_ptrs)
+        _check(load().lgf_batch_graph_create_io(c_void_p(self.h), fh, ph, f, p, c_void_p(cuda_stream)))
 
     def autotune(self, f_ptrs, phi_ptrs, cuda_stream: int = 0):
         f, _a = _ptrs(f_ptrs)

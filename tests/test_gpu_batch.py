@@ -221,3 +221,46 @@ def test_batch_autotune_choices_and_results(L, table8, inst):
         assert torch.equal(phi, phis[i]), f"instance {i}"
         assert (phi - ref).abs().max() <= 1e-10 * ref.abs().max()
     b.close()
+
+
+def test_graph_with_host_transfers_matches_device_graph(L, table8, inst):
+    """lgf_batch_graph_create_io: the sources come from pinned host memory and the results go back to it
+    inside the graph; the results equal those of the device-only graph, bit for bit, on every replay."""
+    b, meshes = make_batch(L, table8, inst)
+    host_f = [torch.from_numpy(f).pin_memory() for _, f, _ in inst]
+    host_phi = [torch.full_like(h, float("nan")).pin_memory() for h in host_f]
+    dev_f = [torch.zeros(h.shape, dtype=h.dtype, device="cuda") for h in host_f]
+    dev_phi = [torch.zeros_like(d) for d in dev_f]
+    s = torch.cuda.Stream()
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    b.graph_create_io(ptr(host_f), ptr(host_phi), ptr(dev_f), ptr(dev_phi), s.cuda_stream)
+    ref_f = [h.cuda() for h in host_f]
+    ref_phi = [torch.zeros_like(d) for d in ref_f]
+    b2, _ = make_batch(L, table8, inst)
+    b2.graph_create(1, ptr(ref_f), ptr(ref_phi), None, None, s.cuda_stream)
+    b2.graph_launch(s.cuda_stream)
+    s.synchronize()
+    for rep in range(2):
+        for h in host_phi:
+            h.fill_(float("nan"))
+        for d in dev_f:
+            d.zero_()
+        torch.cuda.synchronize()
+        b.graph_launch(s.cuda_stream)
+        s.synchronize()
+        for i in range(len(inst)):
+            assert torch.equal(host_phi[i], ref_phi[i].cpu()), (rep, i)
+    b.close()
+    b2.close()
+
+
+def test_graph_with_host_transfers_rejects_pageable_memory(L, table8, inst):
+    b, _ = make_batch(L, table8, inst)
+    pageable = [torch.from_numpy(f.copy()) for _, f, _ in inst]
+    dev = [torch.zeros(h.shape, dtype=h.dtype, device="cuda") for h in pageable]
+    ptr = lambda ts: [t.data_ptr() for t in ts]
+    s = torch.cuda.Stream()
+    with pytest.raises(L.LgfError) as e:
+        b.graph_create_io(ptr(pageable), ptr(pageable), ptr(dev), ptr(dev), s.cuda_stream)
+    assert e.value.status == L.LGF_E_INVALID_ARG
+    b.close()
