@@ -429,8 +429,7 @@ __global__ void __launch_bounds__(256) k_bdft_dense(const cx<double> *__restrict
 //   5  z lines      : FFT_z, conjugate, conjugate twiddle    -> global Y
 // (the inverse is conj(FFT(conj(.))), so one FFT body serves every step: small code, no
 // instruction-cache stalls).  Four barriers, one shared store and load per cell and step.  Ghat is stored
-// per block as [x][z][y] so the x lines of step 2 read it coalesced, on the blocks K1 <= P/2 only (it is
-// even in every axis; box_spec.cu).  Shared memory: B^3 complex with
+// per block as [x][z][y] so the x lines of step 2 read it coalesced.  Shared memory: B^3 complex with
 // rows padded to B + 1 (every line direction conflict-free).  Without MULTIPLY (kernel-spectrum
 // generation) the real part of step 2 goes to `kout` in the same [x][z][y] order.  The per-cell twiddle
 // is one load from a table of W_L^n, L = lcm of the three lattice periods, at an integer exponent.
@@ -580,31 +579,10 @@ __global__ void __launch_bounds__(mid_threads<R, B>(), 512 / (B * B)) k_box_mid(
 #pragma unroll
         for (int j = 0; j < NV; ++j) kout[kb * B3 + out_idx(j) * B2 + t] = v[j].re;
       } else {
-        // Ghat is kept on the blocks K1 <= P/2 per axis (even in every axis): K1 > P/2 reads block P - K1
-        // with that axis's local frequency reflected, K2 -> B - 1 - K2 (here (K2y, K2z) = (l0, l1))
-        // (32-bit offsets: a kept spectrum has at most 17^3 B^3 values)
-        const int hx = g.P[0] / 2, hy = g.P[1] / 2, hz = g.P[2] / 2;
-        const bool rx = k1x > hx;
-        const int sx = rx ? g.P[0] - k1x : k1x, sy = k1y > hy ? g.P[1] - k1y : k1y;
-        const int sz = k1z > hz ? g.P[2] - k1z : k1z;
-        const int g0 = (sx + (hx + 1) * (sy + (hy + 1) * sz)) * B3 + (k1z > hz ? B - 1 - l1 : l1) * B +
-                       (k1y > hy ? B - 1 - l0 : l0);
-        if constexpr (SPLIT) {  // the reflected K2x may sit in the other half's registers: reflect the read
 #pragma unroll
-          for (int j = 0; j < NV; ++j) {
-            const int kx2 = rx ? B - 1 - out_idx(j) : out_idx(j);
-            const R gk = ld_stream(Gh + (g0 + kx2 * B2));  // read once per solve
-            v[j] = cx<R>{v[j].re * gk, -(v[j].im * gk)};
-          }
-        } else {  // the whole x line: constant-offset loads, the reflection a register select
-          R gk[B];
-#pragma unroll
-          for (int j = 0; j < B; ++j) gk[j] = ld_stream(Gh + (g0 + j * B2));  // read once per solve
-#pragma unroll
-          for (int j = 0; j < B; ++j) {
-            const R gj = rx ? gk[B - 1 - j] : gk[j];
-            v[j] = cx<R>{v[j].re * gj, -(v[j].im * gj)};
-          }
+        for (int j = 0; j < NV; ++j) {
+          const R gk = ld_stream(Gh + kb * B3 + out_idx(j) * B2 + t);  // read once per solve
+          v[j] = cx<R>{v[j].re * gk, -(v[j].im * gk)};
         }
       }
       continue;

@@ -2,11 +2,8 @@
 //
 // For a box of nb blocks per axis (periodic lattice Pc = 2 nb B), Ghat[K1][K2] is the Pc^3 DFT of the
 // circularly laid out unit-lattice LGF (cell n holds G(d), d = n for n <= Pc/2, n - Pc above), in the
-// four-step order of box.cuh.  G is real and even so Ghat is real and even: Ghat[K] = Ghat[Pc - K] per
-// axis.  With K = K1 + P K2, the block K1 > P/2 holds the values of block P - K1 at K2 -> B - 1 - K2, so only
-// the blocks K1 <= P/2 are kept ((P/2 + 1)^3 of P^3, about an eighth).  Computed once in FP64 (dense
-// block-index DFTs + the local FFT of k_box_mid) on the full lattice, then the kept blocks are copied out in
-// FP64, FP32 and double-float.
+// four-step order of box.cuh.  G is real and even so Ghat is real.  Computed once in FP64 (dense
+// block-index DFTs + the local FFT of k_box_mid), then rounded to FP32 and split into double-float.
 #include <math.h>
 #include <string.h>
 
@@ -18,20 +15,12 @@
 
 namespace lgf {
 
-// Kept block (kx, ky, kz) <= P/2 of the full spectrum gfull ([P^3 blocks][B3]) -> the three copies;
-// grid (kept blocks, B3 / 256), 256 threads.
-__global__ void k_spec_keep(const double *__restrict__ gfull, BoxGeom g, int B3, double *__restrict__ g64,
-                            float *__restrict__ g32, df *__restrict__ gdf) {
-  const int hx = g.P[0] / 2 + 1, hy = g.P[1] / 2 + 1;
-  const int sb = blockIdx.x, kx = sb % hx, ky = (sb / hx) % hy, kz = sb / (hx * hy);
-  const int64_t kb = kx + (int64_t)g.P[0] * (ky + (int64_t)g.P[1] * kz);
-  for (int m = blockIdx.y * blockDim.x + threadIdx.x; m < B3; m += gridDim.y * blockDim.x) {
-    const double v = gfull[kb * B3 + m];
-    const int64_t o = (int64_t)sb * B3 + m;
-    g64[o] = v;
-    g32[o] = (float)v;
-    gdf[o] = df_make(v);
-  }
+__global__ void k_spec_convert(const double *__restrict__ g, int64_t n, float *__restrict__ g32,
+                               df *__restrict__ gdf) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (g32) g32[i] = (float)g[i];
+  if (gdf) gdf[i] = df_make(g[i]);
 }
 
 __global__ void k_tw_convert(const double *__restrict__ c, const double *__restrict__ s, int n,
@@ -140,26 +129,22 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
   g.nc = 1;
   const int64_t nblk = (int64_t)g.P[0] * g.P[1] * g.P[2];
   const int64_t n = nblk * B3;
-  const int64_t nkeep = (int64_t)(g.P[0] / 2 + 1) * (g.P[1] / 2 + 1) * (g.P[2] / 2 + 1);
   cx<double> *Y0 = nullptr, *Y1 = nullptr, *wP[3] = {nullptr, nullptr, nullptr};
-  double *dc = nullptr, *ds = nullptr, *gfull = nullptr;
+  double *dc = nullptr, *ds = nullptr;
   auto fail = [&](int code, const char *what) {
     cudaFree(Y0);
     cudaFree(Y1);
-    cudaFree(gfull);
     for (int a = 0; a < 3; ++a) cudaFree(wP[a]);
     cudaFree(dc);
     cudaFree(ds);
     cudaGetLastError();
     return set_error(code, "box spectrum: %s", what);
   };
-  if (cudaMalloc(&Y0, sizeof(cx<double>) * n) || cudaMalloc(&Y1, sizeof(cx<double>) * n) ||
-      cudaMalloc(&gfull, sizeof(double) * n))
-    return fail(LGF_E_OOM, "scratch");
-  if (cudaMalloc(&S->g64, sizeof(double) * nkeep * B3) || cudaMalloc(&S->g32, sizeof(float) * nkeep * B3) ||
-      cudaMalloc(&S->gdf, sizeof(df) * nkeep * B3))
+  if (cudaMalloc(&Y0, sizeof(cx<double>) * n) || cudaMalloc(&Y1, sizeof(cx<double>) * n)) return fail(LGF_E_OOM, "scratch");
+  if (cudaMalloc(&S->g64, sizeof(double) * n) || cudaMalloc(&S->g32, sizeof(float) * n) ||
+      cudaMalloc(&S->gdf, sizeof(df) * n))
     return fail(LGF_E_OOM, "spectrum");
-  S->bytes = nkeep * B3 * (8 + 4 + 8);
+  S->bytes = n * (8 + 4 + 8);
   // per-axis tables: W_P (block DFT) and W_Pc (four-step twiddle)
   for (int a = 0; a < 3; ++a) {
     std::vector<double> c, s;
@@ -207,14 +192,12 @@ static int gen_spectrum(lgf_table *t, BoxSpec *S, cudaStream_t st) {
   const size_t sm = sizeof(cx<double>) * (size_t)B * B * (B + 1);
   cudaFuncSetAttribute(k_box_mid<double, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_box_mid<double, B, false><<<dim3((unsigned)nblk, 1), mid_threads<double, B>(), sm, st>>>(
-      Y0, 0, nullptr, g, S->twl64, S->twL, make_int3(S->twf[0], S->twf[1], S->twf[2]), make_tw64<double>(), gfull);
-  k_spec_keep<<<dim3((unsigned)nkeep, (B3 + 255) / 256), 256, 0, st>>>(gfull, g, B3, S->g64, S->g32, S->gdf);
+      Y0, 0, nullptr, g, S->twl64, S->twL, make_int3(S->twf[0], S->twf[1], S->twf[2]), make_tw64<double>(), S->g64);
+  k_spec_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S->g64, n, S->g32, S->gdf);
   cudaError_t e = cudaStreamSynchronize(st);
   cudaFree(Y0);
   cudaFree(Y1);
-  cudaFree(gfull);
   for (int a = 0; a < 3; ++a) cudaFree(wP[a]);
-  gfull = nullptr;
   Y0 = Y1 = nullptr;
   wP[0] = wP[1] = wP[2] = nullptr;
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess)

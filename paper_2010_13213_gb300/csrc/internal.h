@@ -105,10 +105,7 @@ struct TcMat {
 
 struct BoxSpec {
   int nb[3] = {0, 0, 0};
-  // Real spectrum on the block frequencies K1 in [0, P/2] per axis only ([Kz][Ky][Kx] over (P/2 + 1)^3
-  // blocks, each [B^3] as k_box_mid reads it): Ghat is even in every axis, and the block K1 > P/2 holds the
-  // values of block P - K1 with the local frequency K2 of that axis reflected to B - 1 - K2.
-  double *g64 = nullptr;
+  double *g64 = nullptr;  // [P^3 blocks][B^3] real spectrum, FP64
   float *g32 = nullptr;
   df *gdf = nullptr;
   // four-step twiddles: W_L^n, n < L = lcm(Pcx, Pcy, Pcz) (Pc = P B cells per axis); the twiddle of a
