@@ -373,17 +373,19 @@ def batch_stage_heat(L, torch, dev, steps, warmup, world):
                 nstreams=16)
     bs = torch.cuda.Stream(dev)
     ptr = lambda ts: [t.data_ptr() for t in ts]
+    b.autotune(ptr(fs), ptr(phis), bs.cuda_stream)  # DFT-pass variant, order and stream count (Poisson stages)
     stage_alpha = [[0.1 / 3.0] * NINST, [0.2 / 3.0] * NINST, [0.1 / 3.0] * NINST]
     b.graph_create(3, ptr(fs), ptr(phis), ptr(gs), ptr(tmps), bs.cuda_stream, alpha_stages=stage_alpha)
     ms = time_calls(torch, lambda: b.graph_launch(bs.cuda_stream), steps, warmup, bs, world=world) / 3.0
     nodes = b.graph_nodes()
+    ns = b.tuning()[0]
     b.close()
     L.lgf_table_destroy(table)
     total = int(sum(cells))
     return {"workload": "the 64 instances, per stage one DF32 Poisson solve and one DF32 heat apply each, three "
                         "stages per graph with per-stage alpha (HERK increments 1/3, 2/3, 1/3 of alpha = 0.1)",
             "ms_per_stage": ms, "value": total / (ms * 1e-3) / 1e6, "unit": "Mcells/s (Poisson target cells)",
-            "graph_nodes": int(nodes), "stages_per_graph": 3}
+            "graph_nodes": int(nodes), "stages_per_graph": 3, "nstreams": ns}
 
 
 # ------------------------------------------------------------------------------------- single configs

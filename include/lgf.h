@@ -365,9 +365,10 @@ int lgf_batch_graph_create_io(lgf_batch *b, const void *const *f_host, void *con
  *        for DF32 / FP32 solves, the tensor-core DFT-GEMM with 5 / 3 digit slices (the fewest that keep the
  *        arithmetic's accuracy), whichever solves the instance faster (three timed solves each);
  *   (ii) the instance order, longest measured solve first, dealt to the least-loaded stream;
- *   (iii) the stream count from {4, 8, 16, 32}, by timing a Poisson stage captured into a graph and
- *        replayed (the fastest of five replays; eager stages when cuda_stream cannot capture, e.g. the
- *        legacy default stream); a larger count is taken only when it is at least 1 % faster.
+ *   (iii) the stream count from {1, 2, 4, 8, 16, 32} (at most ninst), by timing a Poisson stage captured
+ *        into a graph and replayed (the fastest of five replays; eager stages when cuda_stream cannot
+ *        capture, e.g. the legacy default stream); a larger count is taken only when it is at least 1 %
+ *        faster.
  * f_dev / phi_dev: the instances' fields (phi is overwritten).  Synchronises cuda_stream.  A graph captured
  * before the call keeps the old choices; capture after it.
  */

@@ -310,8 +310,8 @@ int lgf_batch_autotune(lgf_batch *b, const void *const *f_dev, void *const *phi_
   int rc = LGF_OK;
   // each candidate is timed as it will run: a Poisson stage captured into a graph and replayed (eager
   // stages when cuda_stream cannot capture, e.g. the legacy default stream)
-  for (int ns : {4, 8, 16, 32}) {
-    if (ns > b->n && ns != 4) continue;
+  for (int ns : {1, 2, 4, 8, 16, 32}) {
+    if (ns > b->n) continue;
     if ((rc = schedule(b, ns))) break;
     // one eager stage creates the workspaces of streams not used before (no allocation while capturing)
     if ((rc = batch_stage(b, f_dev, phi_dev, nullptr, nullptr, st))) break;

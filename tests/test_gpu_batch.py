@@ -204,7 +204,7 @@ def test_batch_autotune_choices_and_results(L, table8, inst):
     ptr = lambda ts: [t.data_ptr() for t in ts]
     b.autotune(ptr(fs), ptr(phis), s.cuda_stream)
     ns, slices, ms = b.tuning()
-    assert ns in (4, 8, 16, 32) and all(x in (0, 5) for x in slices) and all(m > 0 for m in ms)
+    assert ns in (1, 2, 4, 8) and all(x in (0, 5) for x in slices) and all(m > 0 for m in ms)
     b.graph_create(1, ptr(fs), ptr(phis), None, None, s.cuda_stream)
     for t in phis:
         t.zero_()
