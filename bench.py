@@ -287,7 +287,7 @@ def batch_poisson(L, torch, dev, steps, warmup, world, pk, fp64=True, check=True
         if name == "df32":
             # end to end through the C ABI with host buffers: (a) the serial form, every step copies all
             # sources in from pinned host memory on one stream, replays the graph, copies all results out;
-            # (b) lgf_batch_graph_create_io, the same copies inside the graph on the instances' streams
+            # (b) lgf_batch_graph_create_io, the same copies inside the graph on two copy streams
             hin = [h.pin_memory() for h in host]
             hout = [torch.empty_like(h).pin_memory() for h in host]
 
@@ -792,8 +792,8 @@ def run_gpu(args):
             "e2e": {"value": replica_rate(total, ms_e2e, world), "unit": "Mcells/s",
                     "h2d_bytes_per_step": res["e2e_bytes"], "d2h_bytes_per_step": res["e2e_bytes"],
                     "note": "every step: all 64 sources copied in from pinned host memory and all 64 results "
-                            "copied out inside one graph (lgf_batch_graph_create_io: each instance's copies on the "
-                            "stream that solves it, overlapping the other instances' solves)",
+                            "copied out inside one graph (lgf_batch_graph_create_io: two copy streams, each solve "
+                            "waiting for its own source only, so the copies overlap the other instances' solves)",
                     "graph_nodes": res["e2e_nodes"], "results_match_device_graph": res.get("e2e_match"),
                     "serial": {"value": replica_rate(total, ms_e2e_serial, world), "unit": "Mcells/s",
                                "note": "one stream: all copies in, the device graph, all copies out"}},

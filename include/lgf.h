@@ -347,8 +347,9 @@ int lgf_batch_graph_launch(lgf_batch *b, void *cuda_stream);
 
 /*
  * lgf_batch_graph_create_io -- capture one Poisson stage (phi = L^{-1} f per instance, Sec. 3.4) with its
- * host transfers inside the graph: per instance, on the stream that solves it, f_host[i] -> f_dev[i] before
- * the solve and phi_dev[i] -> phi_host[i] after it, so one instance's copies overlap the others' solves.
+ * host transfers inside the graph: f_host[i] -> f_dev[i] on a copy-in stream in the order the solves start,
+ * each solve waiting for its own source only, and phi_dev[i] -> phi_host[i] on a copy-out stream after the
+ * solve, in the order the solves are expected to end, so the copies overlap the other instances' solves.
  *   f_host, phi_host : host [ninst] pointers to PINNED host buffers (cudaHostAlloc or cudaHostRegister),
  *                      each the instance's field bytes (ncomp x its blocks x B^3 x 8 or 4 for the dtype);
  *                      pageable memory is rejected with LGF_E_INVALID_ARG.  Owned by the caller.

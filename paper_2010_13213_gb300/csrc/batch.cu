@@ -33,6 +33,10 @@ struct lgf_batch {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
+  // host transfers (lgf_batch_graph_create_io): one copy-in and one copy-out stream, per-instance events
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_done;
+  cudaEvent_t ev_cin = nullptr, ev_cout = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_stages = 0;
@@ -53,21 +57,59 @@ static size_t field_bytes(const lgf_batch *b, int i) {
   return (size_t)b->ncomp * (size_t)tot * B3 * (b->dtype == LGF_F64 ? 8 : 4);
 }
 
-// One stage over all instances.  With f_host / phi_host (pinned host buffers): each instance's source is
-// copied in before its solve and its result out after it, on the instance's stream.
+// The copy streams and per-instance events of the host-transfer path (created once).
+static int io_resources(lgf_batch *b) {
+  if (b->copy_in) return LGF_OK;
+  auto ev = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess; };
+  b->ev_in.assign(b->n, nullptr);
+  b->ev_done.assign(b->n, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->copy_in, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->copy_out, cudaStreamNonBlocking) == cudaSuccess && ev(&b->ev_cin) &&
+            ev(&b->ev_cout);
+  for (int i = 0; i < b->n && ok; ++i) ok = ev(&b->ev_in[i]) && ev(&b->ev_done[i]);
+  return ok ? LGF_OK : set_error(LGF_E_CUDA, "batch copy stream creation failed");
+}
+
+// One stage over all instances.  With f_host / phi_host (pinned host buffers): the sources are copied in on
+// a copy stream in the order the solves start, each solve waits for its own source only, and the results
+// are copied out on a second copy stream in the order the solves are expected to end (from the measured
+// or block-count weights), so the transfers overlap the solves of the other instances.
 static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, void *const *g, const double *alpha,
                        cudaStream_t st, const void *const *f_host = nullptr, void *const *phi_host = nullptr) {
   if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return set_error(LGF_E_CUDA, "batch fork event failed");
+  const bool io = f_host && phi_host;
+  std::vector<int> by_start, by_end;
+  if (io) {
+    int rc = io_resources(b);
+    if (rc) return rc;
+    const std::vector<double> &w = b->tuned ? b->tuned_ms : b->cost;
+    std::vector<double> t0(b->n, 0.0), t1(b->n, 0.0);
+    for (int s = 0; s < b->nstreams; ++s) {
+      double t = 0.0;
+      for (int i : b->by_stream[s]) t0[i] = t, t += w[i], t1[i] = t;
+    }
+    by_start.resize(b->n);
+    for (int i = 0; i < b->n; ++i) by_start[i] = i;
+    by_end = by_start;
+    std::stable_sort(by_start.begin(), by_start.end(), [&](int a, int c) { return t0[a] < t0[c]; });
+    std::stable_sort(by_end.begin(), by_end.end(), [&](int a, int c) { return t1[a] < t1[c]; });
+    cudaStreamWaitEvent(b->copy_in, b->ev_fork, 0);
+    for (int i : by_start) {
+      if (cudaMemcpyAsync((void *)f[i], f_host[i], field_bytes(b, i), cudaMemcpyHostToDevice, b->copy_in) !=
+          cudaSuccess)
+        return set_error(LGF_E_CUDA, "instance %d: source copy failed", i);
+      cudaEventRecord(b->ev_in[i], b->copy_in);
+    }
+    cudaEventRecord(b->ev_cin, b->copy_in);
+  }
   for (int s = 0; s < b->nstreams; ++s) {
     cudaStream_t ss = b->streams[s];
     cudaStreamWaitEvent(ss, b->ev_fork, 0);
     for (int i : b->by_stream[s]) {
-      if (f_host && cudaMemcpyAsync((void *)f[i], f_host[i], field_bytes(b, i), cudaMemcpyHostToDevice, ss) != cudaSuccess)
-        return set_error(LGF_E_CUDA, "instance %d: source copy failed", i);
+      if (io) cudaStreamWaitEvent(ss, b->ev_in[i], 0);
       int rc = lgf_poisson_solve(b->t, &b->mesh[i], b->ncomp, f[i], phi[i], b->dtype, &b->opts_i[i], nullptr, ss);
       if (rc) return rc;
-      if (phi_host && cudaMemcpyAsync(phi_host[i], phi[i], field_bytes(b, i), cudaMemcpyDeviceToHost, ss) != cudaSuccess)
-        return set_error(LGF_E_CUDA, "instance %d: result copy failed", i);
+      if (io) cudaEventRecord(b->ev_done[i], ss);
       if (g && g[i]) {
         rc = lgf_heat_apply(b->t, &b->mesh[i], b->ncomp, f[i], g[i], b->dtype, alpha ? alpha[i] : b->alpha[i],
                             &b->opts, nullptr, ss);
@@ -76,6 +118,18 @@ static int batch_stage(lgf_batch *b, const void *const *f, void *const *phi, voi
     }
     cudaEventRecord(b->ev_join[s], ss);
     cudaStreamWaitEvent(st, b->ev_join[s], 0);
+  }
+  if (io) {
+    cudaStreamWaitEvent(b->copy_out, b->ev_fork, 0);
+    for (int i : by_end) {
+      cudaStreamWaitEvent(b->copy_out, b->ev_done[i], 0);
+      if (cudaMemcpyAsync(phi_host[i], phi[i], field_bytes(b, i), cudaMemcpyDeviceToHost, b->copy_out) !=
+          cudaSuccess)
+        return set_error(LGF_E_CUDA, "instance %d: result copy failed", i);
+    }
+    cudaEventRecord(b->ev_cout, b->copy_out);
+    cudaStreamWaitEvent(st, b->ev_cin, 0);
+    cudaStreamWaitEvent(st, b->ev_cout, 0);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LGF_OK : set_error(LGF_E_CUDA, "batch stage: %s", cudaGetErrorString(e));
@@ -171,6 +225,12 @@ int lgf_batch_destroy(lgf_batch *b) {
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto e : b->ev_join) cudaEventDestroy(e);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->copy_in) cudaStreamDestroy(b->copy_in);
+  if (b->copy_out) cudaStreamDestroy(b->copy_out);
+  for (auto e : b->ev_in) if (e) cudaEventDestroy(e);
+  for (auto e : b->ev_done) if (e) cudaEventDestroy(e);
+  if (b->ev_cin) cudaEventDestroy(b->ev_cin);
+  if (b->ev_cout) cudaEventDestroy(b->ev_cout);
   delete b;
   return LGF_OK;
 }
