@@ -134,6 +134,36 @@ LGF_D R interp_staged(const R *S, int4 bc, int B, int x, int y, int z) {
   return interp_at<R>(x, y, z, [&](int i, int j, int k) { return S[((k - z0) * W + (j - y0)) * W + (i - x0)]; });
 }
 
+// The same interpolation for a whole fine block by separable passes over the staged cube (the weights
+// 3/4, 1/4 per axis factor the 27, 9, 3, 1 / 64 of the eight corners): x into T1[W][W][B], y into
+// T2[W][B][B] (each value renormalised), and z per cell by interp_sep_z.  Three terms' worth of work per
+// fine cell instead of eight.  Called by every thread of the CTA (two barriers).
+template <class R>
+LGF_D void interp_sep_xy(const R *S, R *T1, R *T2, int sh) {
+  const int B = 1 << sh, W = (B >> 1) + 2;
+  for (int t = threadIdx.x; t < W * W * B; t += blockDim.x) {
+    const int lx = t & (B - 1), kj = t >> sh;  // kj = kz W + jy
+    const int ip = (lx >> 1) + 1, iq = (lx & 1) ? ip + 1 : ip - 1;
+    const R *row = S + kj * W;
+    T1[t] = rnorm(radd(rscale(row[ip], 0.75f), rscale(row[iq], 0.25f)));
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < W * B * B; t += blockDim.x) {
+    const int lx = t & (B - 1), ly = (t >> sh) & (B - 1), kz = t >> (2 * sh);
+    const int ip = (ly >> 1) + 1, iq = (ly & 1) ? ip + 1 : ip - 1;
+    const R *col = T1 + kz * W * B + lx;
+    T2[t] = rnorm(radd(rscale(col[ip * B], 0.75f), rscale(col[iq * B], 0.25f)));
+  }
+  __syncthreads();
+}
+template <class R>
+LGF_D R interp_sep_z(const R *T2, int sh, int lx, int ly, int lz) {
+  const int ip = (lz >> 1) + 1, iq = (lz & 1) ? ip + 1 : ip - 1, o = (ly << sh) + lx;
+  return rnorm(radd(rscale(T2[(ip << (2 * sh)) + o], 0.75f), rscale(T2[(iq << (2 * sh)) + o], 0.25f)));
+}
+// Values of T1 and T2 for a block size B
+LGF_HD constexpr int interp_sep_values(int B) { return (B / 2 + 2) * (B / 2 + 2) * B + (B / 2 + 2) * B * B; }
+
 // ------------------------------------------------------------------ restriction (step 1)
 // grid (nU_k, ncomp), 256 threads.  F_k on the caller blocks of level k (BL index = caller index).
 template <class R>
@@ -175,21 +205,21 @@ __global__ void __launch_bounds__(256) k_coarsen_add(LevelDev Lc, R *Fc, int64_t
 }
 
 // ------------------------------------------------------------------ interpolation c_k = P psi_{k-1}
-// grid (nBL_k, ncomp)
+// grid (nBL_k, ncomp), interp_sep_values(B) values of dynamic shared memory (the separable passes)
 template <class R>
 __global__ void __launch_bounds__(256) k_interp(LevelDev L, const int4 *blocks, R *c, int64_t cs, LevelDev Lc,
                                                 const R *psi, int64_t pcs) {
   __shared__ R S[LGF_STAGE_MAX];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, comp = blockIdx.y, sh = L.shift, B = 1 << sh;
-  const int B3 = B * B * B;
-  const int4 bc = blocks[b];
-  stage_coarse<R>(S, Lc, psi, pcs, comp, bc, B);
+  const int B3 = B * B * B, W = (B >> 1) + 2;
+  R *T1 = reinterpret_cast<R *>(smem_raw), *T2 = T1 + W * W * B;
+  stage_coarse<R>(S, Lc, psi, pcs, comp, blocks[b], B);
   __syncthreads();
-  for (int off = threadIdx.x; off < B3; off += blockDim.x) {
-    const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
-              z = (bc.z << sh) + (off >> (2 * sh));
-    c[comp * cs + (int64_t)b * B3 + off] = interp_staged<R>(S, bc, B, x, y, z);
-  }
+  interp_sep_xy<R>(S, T1, T2, sh);
+  for (int off = threadIdx.x; off < B3; off += blockDim.x)
+    c[comp * cs + (int64_t)b * B3 + off] =
+        interp_sep_z<R>(T2, sh, off & (B - 1), (off >> sh) & (B - 1), off >> (2 * sh));
 }
 
 // ------------------------------------------------------------------ coarse Laplacian L_{k-1} psi_{k-1}
@@ -214,6 +244,8 @@ __global__ void __launch_bounds__(512) k_lap(LevelDev L, const int4 *blocks, con
 // ------------------------------------------------------------------ correction source A_k
 // grid (|SA_k|, ncomp), 512 threads.  A[b] for b = SA[i].  k = 0: A = [OM] fhat.  `lpsi` = L_{k-1} psi_{k-1}
 // (k_lap).  With has_coarse: halo_smem<R>(B) bytes of dynamic shared memory (c on the block and its face halo).
+// The interpolation of L_{k-1} psi_{k-1} stays per cell (eight staged corners, only on Omega u Omega^E cells):
+// the separable passes of k_interp would add 33 KB per CTA and halve the resident CTAs (measured slower).
 template <class R>
 __global__ void __launch_bounds__(512) k_correct(LevelDev L, const int4 *blocks, const int32_t *SA,
                                                  const void *f_user, int dtype, int64_t ucs, R *A, int64_t cs,

@@ -247,7 +247,8 @@ static int solve_multi_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void 
     const int nPsi = (int)L.Tpsi.size();
     const int32_t *lists = L.d_lists;
     if (k > 0) {
-      k_interp<R><<<dim3((unsigned)L.BL.size(), ncomp), 256, 0, st>>>(Ld, L.d_BL, c, cs[k], Lc, psi_prev, ccs);
+      k_interp<R><<<dim3((unsigned)L.BL.size(), ncomp), 256, sizeof(R) * (size_t)interp_sep_values(B), st>>>(
+          Ld, L.d_BL, c, cs[k], Lc, psi_prev, ccs);
       LGF_LAUNCH_CHECK("interp");
       tm.mark(PH_INTERP);
     }
