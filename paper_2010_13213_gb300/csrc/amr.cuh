@@ -382,7 +382,8 @@ struct HeatW {
   int r;
 };
 
-// P_k fhat, the level-k reconstruction of the AMR data (Sec. 3.2, Eq. (eq:interp)); grid (|HB_k|, ncomp).
+// P_k fhat, the level-k reconstruction of the AMR data (Sec. 3.2, Eq. (eq:interp)); grid (|HB_k|, ncomp),
+// interp_sep_values(B) values of dynamic shared memory (the separable interpolation passes).
 // The regions partition space, so each cell takes the value of the region that holds it: on the caller's
 // level-k blocks F_k (own values on Omega_k, 8-child means of the finer levels on covered cells); on every
 // other block the interpolation of the level-(k-1) reconstruction Uc (which holds the coarsened level-k data
@@ -392,23 +393,20 @@ __global__ void __launch_bounds__(256) k_heat_build(LevelDev L, const int4 *bloc
                                                     int nU, R *out, int64_t cs, LevelDev Lc, const R *Uc,
                                                     int64_t ucs_c, int has_coarse) {
   __shared__ R S[LGF_STAGE_MAX];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = HB[blockIdx.x], comp = blockIdx.y, sh = L.shift, B = 1 << sh;
-  const int B3 = B * B * B;
-  const int4 bc = blocks[b];
+  const int B3 = B * B * B, W = (B >> 1) + 2;
+  R *T1 = reinterpret_cast<R *>(smem_raw), *T2 = T1 + W * W * B;
   const bool interp = b >= nU && has_coarse;  // the same for the whole CTA
   if (interp) {
-    stage_coarse<R>(S, Lc, Uc, ucs_c, comp, bc, B);
+    stage_coarse<R>(S, Lc, Uc, ucs_c, comp, blocks[b], B);
     __syncthreads();
+    interp_sep_xy<R>(S, T1, T2, sh);
   }
   for (int off = threadIdx.x; off < B3; off += blockDim.x) {
     R v = RT<R>::zero();
-    if (b < nU) {
-      v = F[comp * cs + (int64_t)b * B3 + off];
-    } else if (interp) {
-      const int x = (bc.x << sh) + (off & (B - 1)), y = (bc.y << sh) + ((off >> sh) & (B - 1)),
-                z = (bc.z << sh) + (off >> (2 * sh));
-      v = interp_staged<R>(S, bc, B, x, y, z);
-    }
+    if (b < nU) v = F[comp * cs + (int64_t)b * B3 + off];
+    else if (interp) v = interp_sep_z<R>(T2, sh, off & (B - 1), (off >> sh) & (B - 1), off >> (2 * sh));
     out[comp * cs + (int64_t)b * B3 + off] = v;
   }
 }

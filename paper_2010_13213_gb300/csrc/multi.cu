@@ -604,8 +604,8 @@ static int heat_t(lgf_table *t, const lgf_mesh *m, int ncomp, const void *f, voi
     cudaMemsetAsync(T1, 0, bytes, st);
     cudaMemsetAsync(Ucur, 0, bytes, st);
     // P_k fhat into Ucur: the heat passes' source, kept for the next level's interpolation
-    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, Fall + Foff[k], L.nU, Ucur, cs[k], Lc, Uprev,
-                                                      k > 0 ? cs[k - 1] : 0, k > 0);
+    k_heat_build<R><<<dim3(nHB, ncomp), 256, sizeof(R) * (size_t)interp_sep_values(B), st>>>(
+        Ld, L.d_BL, HB, Fall + Foff[k], L.nU, Ucur, cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
     LGF_LAUNCH_CHECK("heat source");
     tm.mark(PH_INTERP);
     for (int ax = 0; ax < 3; ++ax) {  // x: Ucur -> T1, y: T1 -> T0, z: T0 -> T1
@@ -724,8 +724,8 @@ static int reconstruct_levels(Plan *P, const lgf_mesh *m, int ncomp, const void 
     const int32_t *HB = L.d_lists + L.off_HB;
     const size_t bytes = sizeof(R) * (size_t)ncomp * L.BL.size() * B3;
     cudaMemsetAsync(Ucur, 0, bytes, st);
-    k_heat_build<R><<<dim3(nHB, ncomp), 256, 0, st>>>(Ld, L.d_BL, HB, Fall + Foff[k], L.nU, Ucur, cs[k], Lc, Uprev,
-                                                      k > 0 ? cs[k - 1] : 0, k > 0);
+    k_heat_build<R><<<dim3(nHB, ncomp), 256, sizeof(R) * (size_t)interp_sep_values(B), st>>>(
+        Ld, L.d_BL, HB, Fall + Foff[k], L.nU, Ucur, cs[k], Lc, Uprev, k > 0 ? cs[k - 1] : 0, k > 0);
     LGF_LAUNCH_CHECK("reconstruction");
     if ((rc = consume(k, Ld, (const R *)Ucur, cs[k]))) return rc;
     ++launches;
