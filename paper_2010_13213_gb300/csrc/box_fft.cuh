@@ -122,7 +122,8 @@ struct BFft {
 }  // namespace lgf
 
 // Forward pass for a compile-time block count NB (P = 2 NB): one thread per (line, cell), all P outputs.
-// Grid and arguments as k_bdft_fwd (one chunk: blockIdx.z = field).
+// Grid and arguments as k_bdft_fwd (one chunk: blockIdx.z = field); with gather, NB x NT values of dynamic
+// shared memory.
 template <class R, int B, int NT, int NB>
 __global__ void __launch_bounds__(NT) k_bfft_fwd(const cx<R> *__restrict__ in, cx<R> *__restrict__ out,
                                                  int64_t fstride, BoxGeom g, int ax, int3 ext, BoxTw<R> tw,
@@ -182,17 +183,25 @@ __global__ void __launch_bounds__(NT) k_bfft_fwd(const cx<R> *__restrict__ in, c
     if (ns > 2) add(s2, 2);
     return cx<R>{re, im};
   };
+  // a gathering pass keeps its inputs (read and converted from the caller's fields once) in shared memory
+  // for the odd half, each thread its own NB values (no barrier); the other passes re-read theirs from L1/L2
+  extern __shared__ __align__(16) unsigned char bfft_smem[];
+  cx<R> *SG = reinterpret_cast<cx<R> *>(bfft_smem);
   cx<R> w[NB];
   // even outputs X_{2q} = DFT_NB(x)_q
 #pragma unroll
-  for (int j = 0; j < NB; ++j) w[j] = fetch(j, false);
+  for (int j = 0; j < NB; ++j) {
+    w[j] = fetch(j, false);
+    if (gather) SG[j * NT + threadIdx.x] = w[j];
+  }
   BFft<R, NB, P, false>::run(w, tw);
 #pragma unroll
   for (int q = 0; q < NB; ++q)
     if (!realx || 2 * q <= NB) dst[(2 * q) * bsa] = w[q];
   // odd outputs X_{2q+1} = DFT_NB(x_j W_P^j)_q
 #pragma unroll
-  for (int j = 0; j < NB; ++j) w[j] = bfft_twiddle<R, P, P, false>(fetch(j, true), tw, j);
+  for (int j = 0; j < NB; ++j)
+    w[j] = bfft_twiddle<R, P, P, false>(gather ? SG[j * NT + threadIdx.x] : fetch(j, true), tw, j);
   BFft<R, NB, P, false>::run(w, tw);
 #pragma unroll
   for (int q = 0; q < NB; ++q)

@@ -122,25 +122,26 @@ static int tc_pass(int slices, const cx<R> *in, cx<R> *out, int64_t fstride, con
   return set_error(LGF_E_INVALID_ARG, "%d DFT-GEMM slices are not available for this precision", slices);
 }
 
-// Launch of the FFT passes for a block count 9..16; false for any other count.
+// Launch of the FFT passes for a block count 4..16; false for any other count.  The gathering first forward
+// pass keeps its gathered inputs in shared memory (NB x NT values) for the odd half.
 template <class R, int B, int NT>
 static bool bfft_fwd(int nb, const cx<R> *in, cx<R> *out, int64_t fstride, const BoxGeom &g, int ax, int3 ext,
                      const BoxTw<R> &tw, int gather, int n, int lines, const FwdSpecs &sp, cudaStream_t st) {
   const dim3 grid(B * B * B / NT, lines, n);
   switch (nb) {
-    case 4: k_bfft_fwd<R, B, NT, 4><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 5: k_bfft_fwd<R, B, NT, 5><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 6: k_bfft_fwd<R, B, NT, 6><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 7: k_bfft_fwd<R, B, NT, 7><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 8: k_bfft_fwd<R, B, NT, 8><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 9: k_bfft_fwd<R, B, NT, 9><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 10: k_bfft_fwd<R, B, NT, 10><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 11: k_bfft_fwd<R, B, NT, 11><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 12: k_bfft_fwd<R, B, NT, 12><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 13: k_bfft_fwd<R, B, NT, 13><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 14: k_bfft_fwd<R, B, NT, 14><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 15: k_bfft_fwd<R, B, NT, 15><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
-    case 16: k_bfft_fwd<R, B, NT, 16><<<grid, NT, 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 4: k_bfft_fwd<R, B, NT, 4><<<grid, NT, gather ? 4 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 5: k_bfft_fwd<R, B, NT, 5><<<grid, NT, gather ? 5 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 6: k_bfft_fwd<R, B, NT, 6><<<grid, NT, gather ? 6 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 7: k_bfft_fwd<R, B, NT, 7><<<grid, NT, gather ? 7 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 8: k_bfft_fwd<R, B, NT, 8><<<grid, NT, gather ? 8 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 9: k_bfft_fwd<R, B, NT, 9><<<grid, NT, gather ? 9 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 10: k_bfft_fwd<R, B, NT, 10><<<grid, NT, gather ? 10 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 11: k_bfft_fwd<R, B, NT, 11><<<grid, NT, gather ? 11 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 12: k_bfft_fwd<R, B, NT, 12><<<grid, NT, gather ? 12 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 13: k_bfft_fwd<R, B, NT, 13><<<grid, NT, gather ? 13 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 14: k_bfft_fwd<R, B, NT, 14><<<grid, NT, gather ? 14 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 15: k_bfft_fwd<R, B, NT, 15><<<grid, NT, gather ? 15 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
+    case 16: k_bfft_fwd<R, B, NT, 16><<<grid, NT, gather ? 16 * NT * sizeof(cx<R>) : 0, st>>>(in, out, fstride, g, ax, ext, tw, gather, sp); return true;
     default: return false;
   }
 }
